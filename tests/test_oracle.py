@@ -1,0 +1,270 @@
+"""Pins for the CPU oracle: closed forms, brute force on tiny inputs,
+hand-traced graphs (tests/golden/) and invariants.  Nothing here compares the
+oracle with itself or with the CUDA path."""
+import collections
+import json
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# distances, brute force, medoid, recall
+# --------------------------------------------------------------------------
+
+def test_l2_closed_form():
+    a = np.array([0, 255, 3], np.uint8)
+    b = np.array([255, 0, 1], np.uint8)
+    assert oracle.l2(a, b) == 255 * 255 * 2 + 4
+    x = np.array([0.5, -1.0, 2.0], np.float32)
+    y = np.array([1.5, 1.0, 2.0], np.float32)
+    assert oracle.l2(x, y) == 1.0 + 4.0
+
+
+def _numpy_knn(base, q, k):
+    d = ((base[None, :, :].astype(np.float64) - q[:, None, :].astype(np.float64)) ** 2).sum(-1)
+    ids = np.empty((q.shape[0], k), np.int64)
+    for i in range(q.shape[0]):
+        order = np.lexsort((np.arange(base.shape[0]), d[i]))  # by dist, then id
+        ids[i] = order[:k]
+    return ids, np.take_along_axis(d, ids, 1)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_knn_matches_numpy_with_ties(dtype):
+    rng = np.random.default_rng(0)
+    base = rng.integers(0, 6, size=(300, 8)).astype(dtype)   # many exact ties
+    base[50] = base[7]
+    q = rng.integers(0, 6, size=(20, 8)).astype(dtype)
+    ids, dists = oracle.knn(base, q, 10, threads=3)
+    rid, rd = _numpy_knn(base, q, 10)
+    assert np.array_equal(ids, rid)
+    assert np.array_equal(dists, rd)
+
+
+def test_knn_pads_when_k_exceeds_n():
+    base = np.array([[1], [5]], np.uint8)
+    ids, d = oracle.knn(base, np.array([[4]], np.uint8), 3)
+    assert ids.tolist() == [[1, 0, -1]]
+    assert d[0, :2].tolist() == [1.0, 9.0] and np.isinf(d[0, 2])
+
+
+def test_medoid_matches_numpy():
+    rng = np.random.default_rng(1)
+    base = rng.normal(size=(500, 6)).astype(np.float32)
+    mean = base.astype(np.float64).mean(0)
+    assert oracle.medoid(base) == int(((base - mean) ** 2).sum(1).argmin())
+    # ties go to the lowest id
+    assert oracle.medoid(np.array([[0], [2], [4], [2]], np.uint8)) == 1
+
+
+def test_recall_tie_aware():
+    gt = np.array([[1.0, 2.0, 2.0]])
+    assert oracle.recall_at_k(np.array([[0, 5, 2]]), gt, np.array([[1.0, 2.0, 2.0]]), 3) == 1.0
+    assert oracle.recall_at_k(np.array([[0, 5, -1]]), gt, np.array([[1.0, 2.0, np.inf]]), 3) == 2 / 3
+
+
+# --------------------------------------------------------------------------
+# product quantisation
+# --------------------------------------------------------------------------
+
+def _codebook_from_entries(g):
+    M, d = g["M"], g["d"]
+    cb = np.full((M, 256, d // M), 255.0, np.float32)
+    for m, rows in g["codebook_entries"].items():
+        for c, v in enumerate(rows):
+            cb[int(m), c] = v
+    return cb
+
+
+def test_pq_encode_hand_example_and_ties():
+    cb = np.full((2, 256, 2), 200.0, np.float32)
+    cb[0, 0] = [0, 0]
+    cb[0, 1] = [10, 10]
+    cb[0, 2] = [10, 10]      # duplicate of entry 1: ties go to the lower index
+    cb[1, 5] = [3, 4]
+    x = np.array([[9, 9, 3, 4], [1, 1, 200, 200]], np.uint8)
+    codes = oracle.pq_encode(x, cb)
+    assert codes.tolist() == [[1, 5], [0, 0]]
+
+
+def test_pq_train_single_centroid_closed_forms():
+    rng = np.random.default_rng(2)
+    x = rng.integers(0, 256, size=(1000, 4)).astype(np.uint8)
+    u = np.full((2, 1), 0.3141)
+    # K=1, no Lloyd step: k-means++ seeding picks point floor(u * ns)
+    cb0 = oracle.pq_train(x, 2, u, iters=0, K=1, round_int=False)
+    assert np.array_equal(cb0[0, 0], x[314, :2]) and np.array_equal(cb0[1, 0], x[314, 2:])
+    # K=1, one Lloyd step: the centroid is the mean
+    cb1 = oracle.pq_train(x, 2, u, iters=1, K=1, round_int=False)
+    assert np.allclose(cb1[0, 0], x[:, :2].mean(0), rtol=1e-6)
+    assert np.allclose(cb1[1, 0], x[:, 2:].mean(0), rtol=1e-6)
+
+
+def test_pq_train_recovers_exact_blobs():
+    # four blobs of identical points: k-means must end on them with zero error
+    pts = np.array([[0, 0], [100, 0], [0, 100], [100, 100]], np.uint8)
+    x = np.repeat(pts, 25, axis=0)
+    u = np.array([[0.1, 0.5, 0.7, 0.9]])
+    cb, dist = oracle.pq_train(x, 1, u, iters=3, K=4, return_distortion=True)
+    got = sorted(map(tuple, cb[0].astype(int).tolist()))
+    assert got == sorted(map(tuple, pts.astype(int).tolist()))
+    assert dist[0, -1] == 0.0
+
+
+def test_pq_train_distortion_non_increasing_and_integer_centroids():
+    mx = datagen.sift_like()
+    x = mx.base(3000)
+    cb, dist = oracle.pq_train(x, 32, datagen.kmeanspp_uniforms(mx.seed, 32), iters=6,
+                               return_distortion=True)
+    assert np.all(np.diff(dist, axis=1) <= 1e-9 * dist[:, :1])
+    assert np.array_equal(cb, np.rint(cb))           # u8 data: integer centroids
+    assert cb.min() >= 0 and cb.max() <= 255
+
+
+def test_pq_navigation_hand_worked_star():
+    g = load_golden("pq_star5.json")
+    base = np.array(g["vectors"], np.uint8)
+    adj = np.array(g["adjacency"], np.int32)
+    cb = _codebook_from_entries(g)
+    codes = np.array(g["codes"], np.uint8)
+    q = np.array([g["query"]], np.uint8)
+    ids, d, steps, trace = oracle.search(base, adj, g["entry"], q, g["k"], g["L"], g["depth"],
+                                         codebook=cb, codes=codes, trace_cap=8)
+    assert trace[0, :steps[0]].tolist() == g["expanded"]
+    assert ids[0].tolist() == g["ids"]
+    assert d[0].tolist() == g["dists"]
+
+
+# --------------------------------------------------------------------------
+# search
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_search_hand_traced_line(case):
+    g = load_golden("search_line7.json")
+    c = g["cases"][case]
+    base = np.array(g["vectors"], np.uint8)
+    adj = np.array(g["adjacency"], np.int32)
+    q = np.array([g["query"]], np.uint8)
+    for i, v in g["distances_by_hand"].items():
+        assert oracle.l2(base[int(i)], q[0]) == v
+    ids, d, steps, trace = oracle.search(base, adj, g["entry"], q, g["k"], g["L"], c["depth"],
+                                         trace_cap=16)
+    assert trace[0, :steps[0]].tolist() == c["expanded"]
+    assert steps[0] == c["steps"]
+    assert ids[0].tolist() == c["ids"]
+    assert d[0].tolist() == c["dists"]
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_complete_graph_gives_exact_knn(depth):
+    rng = np.random.default_rng(3)
+    n = 60
+    base = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    adj = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    q = rng.integers(0, 256, size=(12, 16)).astype(np.uint8)
+    ids, d, steps = oracle.search(base, adj, 0, q, 10, n, depth)
+    rid, rd = _numpy_knn(base, q, 10)
+    assert np.array_equal(ids, rid) and np.array_equal(d, rd)
+    assert np.all(steps == n)   # L >= n: every node ends up expanded
+
+
+def test_results_pad_when_fewer_than_k_expanded():
+    base = np.array([[0], [10], [20]], np.uint8)
+    adj = np.array([[1], [-1], [-1]], np.int32)          # node 2 is unreachable
+    ids, d, steps = oracle.search(base, adj, 0, np.array([[20]], np.uint8), 3, 3, 0)
+    assert ids[0].tolist() == [1, 0, -1] and np.isinf(d[0, 2]) and steps[0] == 2
+
+
+def _bfs_reach(adj, s):
+    seen = np.zeros(adj.shape[0], bool)
+    seen[s] = True
+    dq = collections.deque([s])
+    while dq:
+        u = dq.popleft()
+        for w in adj[u]:
+            if w >= 0 and not seen[w]:
+                seen[w] = True
+                dq.append(w)
+    return int(seen.sum())
+
+
+@pytest.fixture(scope="module")
+def small_f32():
+    mx = datagen.inmemory_f32()
+    base = mx.base(3000)
+    q = mx.queries(100)
+    med = oracle.medoid(base)
+    adj = oracle.vamana(base, 24, 1.2, 48, med, datagen.build_order(mx.seed, 3000),
+                        datagen.random_out_neighbours(mx.seed, 3000, 24))
+    gi, gd = oracle.knn(base, q, 10)
+    return base, q, med, adj, gi, gd
+
+
+def test_vamana_graph_invariants(small_f32):
+    base, q, med, adj, _, _ = small_f32
+    assert adj.shape == (3000, 24)
+    for i, row in enumerate(adj):
+        nb = row[row >= 0]
+        assert np.all(row[len(nb):] == -1)           # -1 only as trailing padding
+        assert i not in nb and len(set(nb.tolist())) == len(nb)
+    assert _bfs_reach(adj, med) >= 2990
+
+
+def test_search_invariants(small_f32):
+    base, q, med, adj, gi, gd = small_f32
+    s0 = None
+    recalls = []
+    checked = violations = 0
+    for L in (10, 16, 32, 64):
+        for depth in (0, 1, 2, 4):
+            ids, d, steps, trace = oracle.search(base, adj, med, q, 10, L, depth, trace_cap=1024)
+            assert np.all(np.diff(d, axis=1) >= 0)                    # sorted results
+            for i in range(q.shape[0]):
+                exp = trace[i, :steps[i]]
+                assert len(set(exp.tolist())) == steps[i]             # no node expanded twice
+                assert set(ids[i].tolist()) <= set(exp.tolist())      # results come from expansions
+            if depth == 0:
+                s0 = steps
+                recalls.append(oracle.recall_at_k(ids, gd, d))
+            else:
+                # Step bound of the convergence analysis (Eq. 5): |P_relax| <= (k+1) T.
+                # Its proof is informal and it does not hold for every query (one
+                # query here goes from 22 to 50 steps at L=16, depth 1), so it is
+                # checked as a rate; the mean overhead must stay small.
+                checked += steps.size
+                violations += int(np.sum(steps > (depth + 1) * s0))
+                if depth == 1 and L >= 32:
+                    assert steps.mean() <= 1.10 * s0.mean()
+    assert violations <= 0.01 * checked
+    assert all(b >= a for a, b in zip(recalls, recalls[1:]))          # recall non-decreasing in L
+
+
+@pytest.mark.slow
+def test_inmemory_workload_recall():
+    """Full in-memory float workload: 10k points, R=32, alpha=1.2, L_build=64;
+    recall@10 >= 0.95 at L=64 and a few percent extra steps at depth 1."""
+    mx = datagen.inmemory_f32()
+    base, q = mx.base(10_000), mx.queries(200)
+    med = oracle.medoid(base)
+    adj = oracle.vamana(base, 32, 1.2, 64, med, datagen.build_order(mx.seed, 10_000),
+                        datagen.random_out_neighbours(mx.seed, 10_000, 32))
+    gi, gd = oracle.knn(base, q, 10)
+    ids0, d0, s0 = oracle.search(base, adj, med, q, 10, 64, 0)
+    ids1, d1, s1 = oracle.search(base, adj, med, q, 10, 64, 1)
+    r0, r1 = oracle.recall_at_k(ids0, gd, d0), oracle.recall_at_k(ids1, gd, d1)
+    assert r0 >= 0.95 and abs(r1 - r0) <= 0.01
+    assert 1.0 <= s1.mean() / s0.mean() <= 1.10
+    assert _bfs_reach(adj, med) >= 9990
