@@ -1,0 +1,213 @@
+/*
+ * ann.h -- C ABI of the B300 relaxed-pipeline graph search library (libann).
+ *
+ * The library runs best-first (beam) search over a Vamana-style proximity
+ * graph for batches of queries on one GPU (arXiv 2507.10070, "FlashANNS").
+ * Navigation distances come from product-quantisation (PQ) codes held in HBM
+ * (Section "Graph-Based Vector Indexing", phases 1-2).  The full-precision
+ * node blocks -- vector, degree and neighbour ids -- stay in a slower tier,
+ * host pinned memory by default, which the GPU reads over PCIe itself.  Node
+ * blocks are fetched through the dependency-relaxed pipeline: the node fetched
+ * at step i is chosen before the neighbour distances of up to `depth` earlier
+ * steps are in (Section "Dependency Relaxed Strategy").  Every query runs on
+ * one warp, which issues and waits for its own fetches only; no barrier spans
+ * queries (Section "Resource-Efficient Query-Grained Concurrent I/O Stack").
+ *
+ * Conventions for every entry point:
+ *  - The return value is an ann_status; nothing throws or aborts across the
+ *    ABI.  On failure ann_last_error() gives a message (per host thread).
+ *  - The caller owns every buffer it passes.  "host" means ordinary host
+ *    memory (pinned or pageable); "device" means memory of the current CUDA
+ *    device (e.g. a torch tensor's data_ptr()).
+ *  - Distances are squared Euclidean (L2^2).  Ties are broken by lower id.
+ *  - uint8 data is exact: distances are integers (< 2^24 for d <= 256), so
+ *    results are bit-exact; float32 data uses FP32 arithmetic.
+ */
+#ifndef ANN_H_
+#define ANN_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ANN_OK = 0,
+  ANN_EINVAL = -1,   /* bad argument or malformed index data */
+  ANN_ENOMEM = -2,   /* allocation failed, or a query overflowed its visited set */
+  ANN_ECUDA = -3,    /* a CUDA runtime call failed */
+  ANN_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+  ANN_EBUSY = -5,    /* the index is in use by another search */
+  ANN_EIO = -6       /* file could not be read or written */
+} ann_status;
+
+typedef enum { ANN_U8 = 0, ANN_F32 = 1 } ann_dtype;
+
+/* Where the node blocks (full vector + adjacency) live. */
+typedef enum {
+  ANN_TIER_HOST_PINNED = 0, /* host pinned memory read by the GPU over PCIe (default) */
+  ANN_TIER_HBM = 1          /* device memory */
+} ann_tier;
+
+typedef struct ann_index ann_index; /* opaque, owned by the library */
+
+/*
+ * Index description handed to ann_load_graph.  All pointers are host memory;
+ * the library copies what it needs, so the caller may free them on return.
+ *
+ * Navigation mode:
+ *  - M > 0: PQ navigation.  dtype must be ANN_U8, d % M == 0, (d/M) % 4 == 0,
+ *    M % 16 == 0, M <= 64, and every codebook value an integer in [0, 255]
+ *    (this makes the asymmetric distance an exact integer).  Node blocks go
+ *    to `tier`; codes and codebook go to HBM.
+ *  - M == 0: exact navigation; vectors and adjacency go to HBM (tier must be
+ *    ANN_TIER_HBM).  dtype ANN_U8 or ANN_F32, d % 4 == 0.
+ * Limits: 1 <= n < 2^31, 4 <= d <= 512, 1 <= R <= 128, 0 <= entry < n; every
+ * adjacency id is -1 or in [0, n) and a row ends at its first -1.
+ */
+typedef struct {
+  int64_t n;             /* number of base vectors */
+  int32_t d;             /* dimension */
+  int32_t dtype;         /* ann_dtype */
+  int32_t R;             /* adjacency row length (maximum out-degree) */
+  int32_t entry;         /* entry node of every search (the medoid) */
+  const void* vectors;   /* n*d elements of dtype, row-major */
+  const int32_t* adj;    /* n*R neighbour ids, -1 padded */
+  int32_t M;             /* PQ subspaces; 0 = exact navigation */
+  const float* codebook; /* M*256*(d/M): centroid c of subspace m at (m*256+c)*(d/M) */
+  const uint8_t* codes;  /* n*M PQ codes */
+  int32_t tier;          /* ann_tier of the node blocks */
+} ann_graph_desc;
+
+/* Per-query outputs of a search (each pointer may be NULL).  Memory kind as
+ * the ids/dists of the same call (host for ann_search, device for
+ * ann_search_dev). */
+typedef struct {
+  int32_t* steps;   /* [nq] node blocks fetched and expanded (search steps) */
+  int32_t* status;  /* [nq] ANN_OK, or ANN_ENOMEM if the visited set overflowed */
+  int64_t* t_begin; /* [nq] device global timer (ns) when the query started */
+  int64_t* t_end;   /* [nq] device global timer (ns) when it finished */
+} ann_trace;
+
+/* Totals of one ann_search call, or of the ann_search_dev calls since the
+ * previous ann_sync. */
+typedef struct {
+  int64_t queries;       /* queries searched */
+  int64_t expansions;    /* node blocks fetched and expanded */
+  int64_t block_bytes;   /* bytes of one node block (PQ mode) or adjacency row */
+  int32_t n_failed;      /* queries whose status is not ANN_OK */
+  int32_t first_failed;  /* index of the first failed query, or -1 */
+  float kernel_ms;       /* device time of the last search kernel (ann_search only) */
+} ann_search_stats;
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* ann_last_error(void);
+
+/* Library version string. */
+const char* ann_version(void);
+
+/*
+ * Build an index from a description (see ann_graph_desc).  Validates every
+ * field and adjacency id (ANN_EINVAL), allocates the node-block tier
+ * (cudaHostAlloc, mapped) or HBM copies (ANN_ENOMEM / ANN_ECUDA on failure)
+ * and uploads.  Node block layout: [vector: d*elt bytes][R int32 neighbour
+ * ids, -1 padded][uint32 degree][zero pad to a multiple of 128 bytes].
+ * On success *out owns all of it until ann_free.  Uses the current device.
+ */
+int ann_load_graph(ann_index** out, const ann_graph_desc* desc);
+
+/* Write / read an index as one file (header, vectors, adjacency, codebook,
+ * codes).  ann_load_graph_file returns ANN_EIO on unreadable or truncated
+ * files, then validates like ann_load_graph, placing blocks in `tier`. */
+int ann_save_graph_file(const char* path, const ann_graph_desc* desc);
+int ann_load_graph_file(ann_index** out, const char* path, int32_t tier);
+
+/* Release everything an index owns.  NULL is ignored. */
+void ann_free(ann_index* index);
+
+/* Bytes of one node block of this index, and the number of nodes. */
+int64_t ann_index_block_bytes(const ann_index* index);
+int64_t ann_index_size(const ann_index* index);
+
+/*
+ * Batched search, host buffers (the end-to-end call).
+ *  queries: host, nq*d elements of the index's dtype.
+ *  k: results per query, 1 <= k <= min(L, 256).   L: candidate list size, L <= 4096.
+ *  depth: relaxed-pipeline depth 0..4 (fetches in flight beyond the one being
+ *    expanded); 0 is synchronous best-first search.
+ *  ids, dists: host, nq*k; the k expanded nodes with the smallest exact
+ *    distance, ascending by (distance, id); padded with id -1 and +inf when
+ *    fewer than k nodes were expanded.
+ *  trace: host pointers, may be NULL.  stats: may be NULL.
+ * Blocks until done.  One search at a time per index (ANN_EBUSY otherwise).
+ * Returns ANN_ENOMEM if any query overflowed its visited set (that query's
+ * status says so and its results are what it had found).
+ */
+int ann_search(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
+               int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
+               ann_search_stats* stats);
+
+/*
+ * Same search with device buffers, enqueued on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream); returns once the kernels are launched.
+ * Argument errors are reported at once; per-query failures are recorded on
+ * the device and reported by ann_sync.  Calls on one index must not overlap
+ * on the device (the index's scratch is shared).
+ */
+int ann_search_dev(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
+                   int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
+                   void* stream);
+
+/* Wait for `stream`, then report (and reset) the totals and failures of the
+ * ann_search_dev calls since the previous ann_sync. */
+int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
+
+/*
+ * Train a product quantiser and encode the base (index-construction tooling;
+ * runs on host threads).  The training sample is the first min(n, n_train)
+ * rows.  Per subspace: k-means++ seeding (kpp_uniforms[m*256 + c] is the
+ * uniform draw for centre c; NULL derives the draws from `seed`), then
+ * `iters` Lloyd iterations (empty clusters take the point farthest from its
+ * centroid).  For ANN_U8 the centroids are rounded half-to-even to integers.
+ * codebook_out: host, M*256*(d/M) floats.  codes_out: host, n*M bytes.
+ * nthreads <= 0 uses every hardware thread.
+ */
+int ann_build_pq(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t M,
+                 int64_t n_train, int32_t iters, const double* kpp_uniforms, uint64_t seed,
+                 float* codebook_out, uint8_t* codes_out, int32_t nthreads);
+
+/*
+ * Build a Vamana graph (index-construction tooling; host threads).  Random
+ * out-neighbours to start, then two passes (alpha 1, then `alpha`) of
+ * GreedySearch(entry, x_p, L_build) + RobustPrune + back edges over a random
+ * order of the nodes, in deterministic batches (the result does not depend
+ * on the thread count).  alpha is compared with squared distances.
+ * adj_out: host, n*R ids, -1 padded.  entry_out: the medoid used as entry.
+ */
+int ann_build_graph(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                    float alpha, int32_t L_build, uint64_t seed, int32_t nthreads,
+                    int32_t* adj_out, int32_t* entry_out);
+
+/*
+ * Exact k nearest neighbours by brute force on the GPU (ground truth).
+ * base, queries: host; ids, dists: host, nq*k, ascending by (distance, id).
+ * ANN_U8 distances are exact integers; ANN_F32 uses FP32.
+ */
+int ann_knn_exact(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
+                  int64_t nq, int32_t k, int32_t* ids, float* dists);
+
+/*
+ * Storage-tier read probe: `iters` passes in which every warp of a persistent
+ * grid reads `block_bytes`-sized blocks at random block offsets of a
+ * `bytes`-long region in `tier` (host pinned or HBM), the way the search
+ * fetches node blocks.  Writes the achieved GB/s (10^9 bytes per second).
+ */
+int ann_probe_read_bandwidth(int64_t bytes, int32_t block_bytes, int32_t tier, int32_t iters,
+                             double* gbps_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANN_H_ */

@@ -189,10 +189,12 @@ def vamana(base: np.ndarray, R: int, alpha: float, L_build: int, entry: int,
     return adj
 
 
-def recall_at_k(ids: np.ndarray, gt_dists: np.ndarray, res_dists: np.ndarray, k: int = 10):
-    """Tie-aware recall@k: returned results whose exact distance is <= the
-    k-th true distance, over k (a distance tie at the k-th place may be
-    returned by either id).  Returns the mean over queries."""
-    kth = gt_dists[:, k - 1:k]
-    ok = (res_dists[:, :k] <= kth) & (ids[:, :k] >= 0)
+def recall_at_k(ids, gt_ids, gt_dists, res_dists, k: int = 10) -> float:
+    """Tie-aware recall@k, mean over queries: a returned id counts if it is one
+    of the k true nearest neighbours, or if its distance is <= the k-th true
+    distance (another point tied with a true neighbour).  Capped at k."""
+    ids, gt_ids = np.asarray(ids)[:, :k], np.asarray(gt_ids)[:, :k]
+    kth = np.asarray(gt_dists)[:, k - 1:k]
+    member = (ids[:, :, None] == gt_ids[:, None, :]).any(-1)
+    ok = (member | (np.asarray(res_dists)[:, :k] <= kth)) & (ids >= 0)
     return float(np.minimum(ok.sum(axis=1), k).mean() / k)

@@ -1,0 +1,215 @@
+"""Python binding of libann, the B300 relaxed-pipeline graph search library.
+
+Argument marshalling only: every step of index search runs in the CUDA
+kernels of libann.so (built in-tree by `paper_2507_10070_b300.build`).  There
+is no CPU fallback; importing the binding without the built library, or
+searching without a GPU, raises.
+
+Host arrays are numpy; device buffers are torch CUDA tensors (PyTorch is used
+only for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _abi
+from ._abi import (ANN_F32, ANN_TIER_HBM, ANN_TIER_HOST_PINNED, ANN_U8, AnnError,
+                   GraphDesc, SearchStats, Trace)
+
+__all__ = ["Index", "AnnError", "build_pq", "build_graph", "knn_exact", "probe_read_bandwidth",
+           "recall_at_k", "library_path", "ANN_U8", "ANN_F32", "ANN_TIER_HOST_PINNED",
+           "ANN_TIER_HBM", "save_index"]
+
+
+def library_path() -> str:
+    return _abi.LIB_PATH
+
+
+def _lib():
+    return _abi.lib()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise AnnError(rc, _lib().ann_last_error().decode())
+
+
+def _dtype_code(a: np.ndarray) -> int:
+    if a.dtype == np.uint8:
+        return ANN_U8
+    if a.dtype == np.float32:
+        return ANN_F32
+    raise TypeError(f"vectors must be uint8 or float32, not {a.dtype}")
+
+
+def _c(a, dtype=None):
+    return np.ascontiguousarray(a if dtype is None else np.asarray(a).astype(dtype, copy=False))
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _desc(vectors, adj, entry, codebook, codes, tier):
+    vectors = _c(vectors)
+    adj = _c(adj, np.int32)
+    n, d = vectors.shape
+    assert adj.shape[0] == n
+    M = 0
+    if codebook is not None:
+        codebook = _c(codebook, np.float32)
+        codes = _c(codes, np.uint8)
+        M = codebook.shape[0]
+    keep = (vectors, adj, codebook, codes)
+    desc = GraphDesc(n=n, d=d, dtype=_dtype_code(vectors), R=adj.shape[1], entry=int(entry),
+                     vectors=_p(vectors), adj=_p(adj), M=M, codebook=_p(codebook),
+                     codes=_p(codes), tier=tier)
+    return desc, keep
+
+
+def save_index(path: str, vectors, adj, entry, codebook=None, codes=None):
+    desc, keep = _desc(vectors, adj, entry, codebook, codes, ANN_TIER_HBM)
+    _check(_lib().ann_save_graph_file(path.encode(), ctypes.byref(desc)))
+
+
+class Index:
+    """A loaded index: node blocks in `tier`, PQ codes / vectors in HBM."""
+
+    def __init__(self, vectors=None, adj=None, entry=0, codebook=None, codes=None,
+                 tier: int = ANN_TIER_HOST_PINNED, path: str | None = None):
+        self._h = ctypes.c_void_p()
+        if path is not None:
+            _check(_lib().ann_load_graph_file(ctypes.byref(self._h), path.encode(), tier))
+            with open(path, "rb") as f:
+                hdr = np.frombuffer(f.read(40), dtype=np.uint8)
+            fields = hdr[16:40].view(np.int32)
+            self.d, self.dtype = int(fields[0]), int(fields[1])
+        else:
+            desc, _ = _desc(vectors, adj, entry, codebook, codes, tier)
+            _check(_lib().ann_load_graph(ctypes.byref(self._h), ctypes.byref(desc)))
+            self.d, self.dtype = desc.d, desc.dtype
+        self.n = int(_lib().ann_index_size(self._h))
+        self.block_bytes = int(_lib().ann_index_block_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            _lib().ann_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _np_dtype(self):
+        return np.uint8 if self.dtype == ANN_U8 else np.float32
+
+    def search(self, queries, k: int, L: int, depth: int = 1, trace: bool = False, out=None):
+        """Host-buffer search.  Returns (ids int32 (nq,k), dists float32 (nq,k), stats)
+        plus a dict of per-query arrays (steps, status, t_begin, t_end) if trace.
+        `out` = (ids, dists) preallocated C-contiguous arrays (e.g. views of
+        pinned host memory) to write the results into."""
+        q = _c(queries, self._np_dtype())
+        nq = q.shape[0] if q.ndim == 2 else 0
+        if out is not None:
+            ids, dists = out
+            assert ids.dtype == np.int32 and dists.dtype == np.float32
+            assert ids.shape == (nq, k) and dists.shape == (nq, k)
+            assert ids.flags.c_contiguous and dists.flags.c_contiguous
+        else:
+            ids = np.empty((nq, k), np.int32)
+            dists = np.empty((nq, k), np.float32)
+        stats = SearchStats()
+        tr = tr_arrays = None
+        if trace:
+            tr_arrays = {"steps": np.empty(nq, np.int32), "status": np.empty(nq, np.int32),
+                         "t_begin": np.empty(nq, np.int64), "t_end": np.empty(nq, np.int64)}
+            tr = Trace(**{key: _p(v) for key, v in tr_arrays.items()})
+        rc = _lib().ann_search(self._h, _p(q), nq, k, L, depth, _p(ids), _p(dists),
+                               ctypes.byref(tr) if tr else None, ctypes.byref(stats))
+        if rc != 0 and not (rc == _abi.ANN_ENOMEM and trace):
+            _check(rc)
+        out = (ids, dists, stats)
+        return out + (tr_arrays,) if trace else out
+
+    def search_dev(self, queries, k: int, L: int, depth: int, ids, dists, stream=None,
+                   trace: dict | None = None):
+        """Device-buffer search on a torch stream (asynchronous).  queries, ids,
+        dists (and trace tensors) are contiguous CUDA tensors."""
+        tr = None
+        if trace:
+            tr = Trace(**{key: ctypes.c_void_p(t.data_ptr()) for key, t in trace.items()})
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        nq = queries.shape[0]
+        _check(_lib().ann_search_dev(self._h, ctypes.c_void_p(queries.data_ptr()), nq, k, L, depth,
+                                     ctypes.c_void_p(ids.data_ptr()),
+                                     ctypes.c_void_p(dists.data_ptr()),
+                                     ctypes.byref(tr) if tr else None, st))
+
+    def sync(self, stream=None) -> SearchStats:
+        stats = SearchStats()
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(_lib().ann_sync(self._h, st, ctypes.byref(stats)))
+        return stats
+
+
+def build_pq(base, M: int, n_train: int = 100_000, iters: int = 25, kpp_uniforms=None,
+             seed: int = 0, threads: int = 0):
+    """Train a PQ codebook on the first n_train rows and encode every row.
+    Returns (codebook float32 (M,256,d/M), codes uint8 (n,M))."""
+    base = _c(base)
+    n, d = base.shape
+    cb = np.empty((M, 256, d // M), np.float32)
+    codes = np.empty((n, M), np.uint8)
+    u = None if kpp_uniforms is None else _c(kpp_uniforms, np.float64)
+    _check(_lib().ann_build_pq(_p(base), _dtype_code(base), n, d, M, n_train, iters, _p(u),
+                               ctypes.c_uint64(seed), _p(cb), _p(codes), threads))
+    return cb, codes
+
+
+def build_graph(base, R: int, alpha: float = 1.2, L_build: int = 128, seed: int = 0,
+                threads: int = 0):
+    """Vamana graph on host threads.  Returns (adj int32 (n,R), entry)."""
+    base = _c(base)
+    n, d = base.shape
+    adj = np.empty((n, R), np.int32)
+    entry = ctypes.c_int32(0)
+    _check(_lib().ann_build_graph(_p(base), _dtype_code(base), n, d, R, ctypes.c_float(alpha),
+                                  L_build, ctypes.c_uint64(seed), threads, _p(adj),
+                                  ctypes.byref(entry)))
+    return adj, int(entry.value)
+
+
+def knn_exact(base, queries, k: int):
+    """Brute-force exact kNN on the GPU: (ids int32 (nq,k), dists float32 (nq,k))."""
+    base = _c(base)
+    queries = _c(queries, base.dtype)
+    nq = queries.shape[0]
+    ids = np.empty((nq, k), np.int32)
+    dists = np.empty((nq, k), np.float32)
+    _check(_lib().ann_knn_exact(_p(base), _dtype_code(base), base.shape[0], base.shape[1],
+                                _p(queries), nq, k, _p(ids), _p(dists)))
+    return ids, dists
+
+
+def probe_read_bandwidth(nbytes: int, block_bytes: int = 512, tier: int = ANN_TIER_HOST_PINNED,
+                         iters: int = 64) -> float:
+    """GB/s of random block reads from the storage tier (the search's access pattern)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib().ann_probe_read_bandwidth(nbytes, block_bytes, tier, iters, ctypes.byref(out)))
+    return out.value
+
+
+def recall_at_k(ids, gt_ids, gt_dists, res_dists, k: int = 10) -> float:
+    """Tie-aware recall@k, mean over queries: a returned id counts if it is one
+    of the k true nearest neighbours, or if its distance is <= the k-th true
+    distance (another point tied with a true neighbour).  Capped at k."""
+    ids, gt_ids = np.asarray(ids)[:, :k], np.asarray(gt_ids)[:, :k]
+    kth = np.asarray(gt_dists)[:, k - 1:k]
+    member = (ids[:, :, None] == gt_ids[:, None, :]).any(-1)
+    ok = (member | (np.asarray(res_dists)[:, :k] <= kth)) & (ids >= 0)
+    return float(np.minimum(ok.sum(axis=1), k).mean() / k)

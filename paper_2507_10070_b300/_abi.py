@@ -1,0 +1,93 @@
+"""ctypes declarations mirroring include/ann.h (same names, same layouts)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libann.so")
+
+ANN_OK, ANN_EINVAL, ANN_ENOMEM, ANN_ECUDA, ANN_ETIMEOUT, ANN_EBUSY, ANN_EIO = 0, -1, -2, -3, -4, -5, -6
+ANN_U8, ANN_F32 = 0, 1
+ANN_TIER_HOST_PINNED, ANN_TIER_HBM = 0, 1
+
+STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA",
+                -4: "ANN_ETIMEOUT", -5: "ANN_EBUSY", -6: "ANN_EIO"}
+
+# Every symbol include/ann.h declares.
+EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_file",
+           "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
+           "ann_search", "ann_search_dev", "ann_sync", "ann_build_pq", "ann_build_graph",
+           "ann_knn_exact", "ann_probe_read_bandwidth"]
+
+
+class AnnError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("R", ctypes.c_int32), ("entry", ctypes.c_int32), ("vectors", ctypes.c_void_p),
+                ("adj", ctypes.c_void_p), ("M", ctypes.c_int32), ("codebook", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p), ("tier", ctypes.c_int32)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("t_begin", ctypes.c_void_p), ("t_end", ctypes.c_void_p)]
+
+
+class SearchStats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("expansions", ctypes.c_int64),
+                ("block_bytes", ctypes.c_int64), ("n_failed", ctypes.c_int32),
+                ("first_failed", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libann.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2507_10070_b300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        L.ann_last_error.restype = ctypes.c_char_p
+        L.ann_last_error.argtypes = []
+        L.ann_version.restype = ctypes.c_char_p
+        L.ann_version.argtypes = []
+        L.ann_load_graph.restype = ctypes.c_int
+        L.ann_load_graph.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(GraphDesc)]
+        L.ann_save_graph_file.restype = ctypes.c_int
+        L.ann_save_graph_file.argtypes = [ctypes.c_char_p, ctypes.POINTER(GraphDesc)]
+        L.ann_load_graph_file.restype = ctypes.c_int
+        L.ann_load_graph_file.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p, I32]
+        L.ann_free.restype = None
+        L.ann_free.argtypes = [P]
+        L.ann_index_block_bytes.restype = I64
+        L.ann_index_block_bytes.argtypes = [P]
+        L.ann_index_size.restype = I64
+        L.ann_index_size.argtypes = [P]
+        L.ann_search.restype = ctypes.c_int
+        L.ann_search.argtypes = [P, P, I64, I32, I32, I32, P, P, ctypes.POINTER(Trace),
+                                 ctypes.POINTER(SearchStats)]
+        L.ann_search_dev.restype = ctypes.c_int
+        L.ann_search_dev.argtypes = [P, P, I64, I32, I32, I32, P, P, ctypes.POINTER(Trace), P]
+        L.ann_sync.restype = ctypes.c_int
+        L.ann_sync.argtypes = [P, P, ctypes.POINTER(SearchStats)]
+        L.ann_build_pq.restype = ctypes.c_int
+        L.ann_build_pq.argtypes = [P, I32, I64, I32, I32, I64, I32, P, U64, P, P, I32]
+        L.ann_build_graph.restype = ctypes.c_int
+        L.ann_build_graph.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, I32, P,
+                                      ctypes.POINTER(ctypes.c_int32)]
+        L.ann_knn_exact.restype = ctypes.c_int
+        L.ann_knn_exact.argtypes = [P, I32, I64, I32, P, I64, I32, P, P]
+        L.ann_probe_read_bandwidth.restype = ctypes.c_int
+        L.ann_probe_read_bandwidth.argtypes = [I64, I32, I32, I32, ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib

@@ -1,0 +1,122 @@
+// Internal declarations of libann (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "../../include/ann.h"
+
+namespace ann {
+
+// Navigation / fetch modes of the search kernel.
+enum Mode : int {
+  kModePqU8 = 0,     // PQ navigation, node blocks in the storage tier (uint8 data)
+  kModeExactU8 = 1,  // exact navigation on uint8 vectors in HBM
+  kModeExactF32 = 2  // exact navigation on float32 vectors in HBM
+};
+
+constexpr int kMaxL = 4096;
+constexpr int kMaxDepth = 4;
+constexpr int kMaxR = 128;
+constexpr int kMaxD = 512;
+constexpr int kMaxM = 64;
+
+// Everything one launch of the search kernel reads or writes.
+struct SearchArgs {
+  // index
+  int32_t n, d, R, entry, M, dsub;
+  const uint8_t* blocks;    // PQ mode: n node blocks (host-mapped or HBM)
+  int32_t block_bytes;      // bytes per node block (multiple of 16)
+  int32_t ids_off;          // byte offset of the neighbour ids in a block
+  int32_t deg_off;          // byte offset of the degree in a block
+  const uint8_t* codes;     // PQ mode: n*M codes (HBM)
+  const uint32_t* cb_words; // PQ mode: M*256*(dsub/4) words, 4 uint8 coordinates each
+  const void* vectors;      // exact modes: n*d elements (HBM)
+  const int32_t* adj;       // exact modes: n*adj_stride ids (HBM)
+  int32_t adj_stride;       // ids per adjacency row (multiple of 4)
+  // batch
+  const void* queries;
+  int32_t nq, k, L, depth;
+  int32_t* ids;
+  float* dists;
+  int32_t* steps;
+  int32_t* status;
+  int64_t* t_begin;
+  int64_t* t_end;
+  // scratch
+  uint32_t* vis;            // per-warp open-addressing visited tables, all zero between queries
+  int32_t vis_log2;         // log2 of the table capacity per warp
+  int32_t* counters;        // [0] next query, [1] failed queries, [2] first failed query
+  unsigned long long* expansions;  // running total of expansions
+};
+
+// Launch geometry and shared-memory layout derived from the arguments.
+struct SearchPlan {
+  int mode;
+  int nb;              // neighbour slots per lane: ceil(R/32) rounded to 1, 2 or 4
+  int smem_per_warp;   // bytes
+  int warps_per_block;
+  int blocks;          // grid size (persistent)
+  int vis_log2;
+};
+
+// Per-warp shared-memory layout (byte offsets), identical on host and device.
+struct WarpSmem {
+  int lut, ring, q, keys_a, keys_b, flags_a, flags_b, res, cand, ring_key, total;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int slot_bytes,
+                                                     int depth, int L, int k, int nb) {
+  WarpSmem s;
+  int off = 0;
+  s.lut = off;
+  off += (mode == kModePqU8) ? M * 256 * 4 : 0;
+  off = align_up(off, 16);
+  s.ring = off;
+  off += (depth + 1) * slot_bytes;
+  off = align_up(off, 16);
+  s.q = off;
+  off += (mode == kModeExactF32) ? d * 4 : d;
+  off = align_up(off, 16);
+  s.keys_a = off;
+  off += L * 8;
+  s.keys_b = off;
+  off += L * 8;
+  s.res = off;
+  off += k * 8;
+  s.cand = off;
+  off += 32 * nb * 8;
+  s.ring_key = off;
+  off += (depth + 1) * 8;
+  s.flags_a = off;
+  off += align_up(L, 16);
+  s.flags_b = off;
+  off += align_up(L, 16);
+  s.total = align_up(off, 128);
+  return s;
+}
+
+// Plans and launches one batched search.  Returns cudaSuccess or the error.
+cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
+                        int64_t nq, SearchPlan* plan);
+cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream);
+
+// Storage-tier read probe kernel launcher.
+cudaError_t launch_read_probe(const uint8_t* region, int64_t nblocks, int block_bytes, int iters,
+                              unsigned long long* sink, cudaStream_t stream, float* ms_out,
+                              int64_t* bytes_out);
+
+// Brute-force exact kNN (device buffers).
+cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, const void* queries,
+                             int64_t nq, int k, int32_t* ids, float* dists, cudaStream_t stream);
+
+// Error reporting (thread-local message).
+int set_error(int status, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+}  // namespace ann

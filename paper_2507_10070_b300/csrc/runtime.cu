@@ -1,0 +1,611 @@
+// libann host runtime: the C ABI of include/ann.h.
+//
+// Owns the index (node-block tier in host pinned memory or HBM, PQ codes and
+// codebook in HBM, exact-mode vectors/adjacency in HBM), the per-index search
+// scratch (visited tables, counters, staging buffers for host calls) and the
+// launches of the search kernel.  No step of the search runs on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ann_internal.h"
+
+namespace ann {
+
+static thread_local std::string g_err;
+
+int set_error(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return status;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(ANN_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(ANN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace ann
+
+using namespace ann;
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (p && cap >= bytes) return cudaSuccess;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 1);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  void release() {
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct ann_index {
+  int64_t n = 0;
+  int d = 0, dtype = 0, R = 0, entry = 0, M = 0, dsub = 0, tier = 0, mode = 0;
+  int block_bytes = 0, ids_off = 0, deg_off = 0, adj_stride = 0;
+  uint8_t* blocks_host = nullptr;  // pinned host tier
+  uint8_t* blocks_dev = nullptr;   // device-visible address of the blocks
+  bool blocks_in_hbm = false;
+  uint8_t* codes = nullptr;
+  uint32_t* cb_words = nullptr;
+  void* vectors = nullptr;
+  int32_t* adj = nullptr;
+  // scratch
+  uint32_t* vis = nullptr;
+  size_t vis_words = 0;
+  int32_t* counters = nullptr;              // device [4]
+  unsigned long long* expansions = nullptr; // device [1]
+  int64_t pending_queries = 0;              // ann_search_dev calls since ann_sync
+  // host-call staging (grow-only device buffers)
+  cudaStream_t stream = nullptr;
+  DevBuf q_stage, ids_stage, dists_stage, steps_stage, status_stage, tb_stage, te_stage;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::atomic<int> busy{0};
+};
+
+namespace {
+
+int elt_size(int dtype) { return dtype == ANN_U8 ? 1 : 4; }
+
+void release(ann_index* ix) {
+  if (!ix) return;
+  if (ix->blocks_host) cudaFreeHost(ix->blocks_host);
+  if (ix->blocks_in_hbm && ix->blocks_dev) cudaFree(ix->blocks_dev);
+  cudaFree(ix->codes);
+  cudaFree(ix->cb_words);
+  cudaFree(ix->vectors);
+  cudaFree(ix->adj);
+  cudaFree(ix->vis);
+  cudaFree(ix->counters);
+  cudaFree(ix->expansions);
+  for (DevBuf* b : {&ix->q_stage, &ix->ids_stage, &ix->dists_stage, &ix->steps_stage,
+                    &ix->status_stage, &ix->tb_stage, &ix->te_stage})
+    b->release();
+  if (ix->ev0) cudaEventDestroy(ix->ev0);
+  if (ix->ev1) cudaEventDestroy(ix->ev1);
+  if (ix->stream) cudaStreamDestroy(ix->stream);
+  delete ix;
+}
+
+int validate_desc(const ann_graph_desc* g) {
+  if (!g) return set_error(ANN_EINVAL, "ann_load_graph: desc is NULL");
+  if (g->n < 1 || g->n >= INT32_MAX) return set_error(ANN_EINVAL, "n=%lld out of range", (long long)g->n);
+  if (g->d < 4 || g->d > kMaxD || g->d % 4) return set_error(ANN_EINVAL, "d=%d must be a multiple of 4 in [4,%d]", g->d, kMaxD);
+  if (g->dtype != ANN_U8 && g->dtype != ANN_F32) return set_error(ANN_EINVAL, "unknown dtype %d", g->dtype);
+  if (g->R < 1 || g->R > kMaxR) return set_error(ANN_EINVAL, "R=%d out of range [1,%d]", g->R, kMaxR);
+  if (g->entry < 0 || g->entry >= g->n) return set_error(ANN_EINVAL, "entry %d out of range", g->entry);
+  if (!g->vectors || !g->adj) return set_error(ANN_EINVAL, "vectors and adj are required");
+  if (g->tier != ANN_TIER_HOST_PINNED && g->tier != ANN_TIER_HBM) return set_error(ANN_EINVAL, "unknown tier %d", g->tier);
+  if (g->M < 0) return set_error(ANN_EINVAL, "M=%d < 0", g->M);
+  if (g->M > 0) {
+    if (g->dtype != ANN_U8) return set_error(ANN_EINVAL, "PQ navigation needs uint8 data");
+    if (g->M % 16 || g->M > kMaxM || g->d % g->M || (g->d / g->M) % 4)
+      return set_error(ANN_EINVAL, "PQ needs M %% 16 == 0, M <= %d, d %% M == 0, (d/M) %% 4 == 0 (d=%d, M=%d)", kMaxM, g->d, g->M);
+    if (!g->codebook || !g->codes) return set_error(ANN_EINVAL, "PQ navigation needs codebook and codes");
+    const int64_t ncb = (int64_t)g->M * 256 * (g->d / g->M);
+    for (int64_t i = 0; i < ncb; ++i) {
+      const float v = g->codebook[i];
+      if (!(v >= 0.f && v <= 255.f) || v != std::floor(v))
+        return set_error(ANN_EINVAL, "codebook value %g at %lld is not an integer in [0,255]", v, (long long)i);
+    }
+  } else if (g->tier != ANN_TIER_HBM) {
+    return set_error(ANN_EINVAL, "exact navigation keeps vectors in HBM: use ANN_TIER_HBM");
+  }
+  for (int64_t i = 0; i < g->n * g->R; ++i) {
+    const int32_t v = g->adj[i];
+    if (v < -1 || v >= g->n) return set_error(ANN_EINVAL, "adjacency id %d at row %lld out of range", v, (long long)(i / g->R));
+  }
+  return ANN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ann_last_error(void) { return g_err.c_str(); }
+
+const char* ann_version(void) { return "libann 0.1 (sm_103a)"; }
+
+int64_t ann_index_block_bytes(const ann_index* ix) { return ix ? ix->block_bytes : 0; }
+int64_t ann_index_size(const ann_index* ix) { return ix ? ix->n : 0; }
+
+void ann_free(ann_index* ix) { release(ix); }
+
+int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
+  if (!out) return set_error(ANN_EINVAL, "ann_load_graph: out is NULL");
+  *out = nullptr;
+  int rc = validate_desc(g);
+  if (rc != ANN_OK) return rc;
+  ann_index* ix = new ann_index();
+  ix->n = g->n;
+  ix->d = g->d;
+  ix->dtype = g->dtype;
+  ix->R = g->R;
+  ix->entry = g->entry;
+  ix->M = g->M;
+  ix->dsub = g->M > 0 ? g->d / g->M : 0;
+  ix->tier = g->tier;
+  ix->mode = g->M > 0 ? kModePqU8 : (g->dtype == ANN_U8 ? kModeExactU8 : kModeExactF32);
+  const int64_t n = g->n;
+  const int R = g->R, d = g->d;
+  cudaError_t e;
+#define ANN_TRY(call, what)                   \
+  do {                                        \
+    e = (call);                               \
+    if (e != cudaSuccess) {                   \
+      release(ix);                            \
+      return cuda_error(e, what);             \
+    }                                         \
+  } while (0)
+  ANN_TRY(cudaStreamCreateWithFlags(&ix->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  ANN_TRY(cudaEventCreate(&ix->ev0), "cudaEventCreate");
+  ANN_TRY(cudaEventCreate(&ix->ev1), "cudaEventCreate");
+  ANN_TRY(cudaMalloc(&ix->counters, 4 * sizeof(int32_t)), "cudaMalloc counters");
+  ANN_TRY(cudaMalloc(&ix->expansions, sizeof(unsigned long long)), "cudaMalloc counters");
+  {
+    const int32_t init[4] = {0, 0, INT32_MAX, 0};
+    ANN_TRY(cudaMemcpy(ix->counters, init, sizeof(init), cudaMemcpyHostToDevice), "upload counters");
+    ANN_TRY(cudaMemset(ix->expansions, 0, sizeof(unsigned long long)), "cudaMemset");
+  }
+  if (ix->mode == kModePqU8) {
+    // Node block: [vector d bytes][R int32 ids][uint32 degree][zero pad to 128 B]
+    ix->ids_off = d;
+    ix->deg_off = d + 4 * R;
+    ix->block_bytes = align_up(d + 4 * R + 4, 128);
+    const size_t total = (size_t)n * ix->block_bytes;
+    std::vector<uint8_t> tmp;
+    uint8_t* dst;
+    if (g->tier == ANN_TIER_HOST_PINNED) {
+      ANN_TRY(cudaHostAlloc(reinterpret_cast<void**>(&ix->blocks_host), total,
+                            cudaHostAllocMapped | cudaHostAllocPortable), "cudaHostAlloc node blocks");
+      dst = ix->blocks_host;
+    } else {
+      tmp.resize(total);
+      dst = tmp.data();
+    }
+    const uint8_t* vec = static_cast<const uint8_t*>(g->vectors);
+    for (int64_t i = 0; i < n; ++i) {
+      uint8_t* b = dst + (size_t)i * ix->block_bytes;
+      std::memset(b, 0, ix->block_bytes);
+      std::memcpy(b, vec + (size_t)i * d, d);
+      int32_t* ids = reinterpret_cast<int32_t*>(b + ix->ids_off);
+      uint32_t deg = 0;
+      for (int j = 0; j < R; ++j) {
+        const int32_t v = g->adj[(size_t)i * R + j];
+        if (v < 0) break;
+        ids[deg++] = v;
+      }
+      for (int j = deg; j < R; ++j) ids[j] = -1;
+      std::memcpy(b + ix->deg_off, &deg, 4);
+    }
+    if (g->tier == ANN_TIER_HOST_PINNED) {
+      ANN_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ix->blocks_dev), ix->blocks_host, 0),
+              "cudaHostGetDevicePointer");
+    } else {
+      ANN_TRY(cudaMalloc(&ix->blocks_dev, total), "cudaMalloc node blocks");
+      ix->blocks_in_hbm = true;
+      ANN_TRY(cudaMemcpy(ix->blocks_dev, tmp.data(), total, cudaMemcpyHostToDevice), "upload node blocks");
+    }
+    ANN_TRY(cudaMalloc(&ix->codes, (size_t)n * g->M), "cudaMalloc codes");
+    ANN_TRY(cudaMemcpy(ix->codes, g->codes, (size_t)n * g->M, cudaMemcpyHostToDevice), "upload codes");
+    const int wps = ix->dsub / 4;
+    std::vector<uint32_t> words((size_t)g->M * 256 * wps);
+    for (int m = 0; m < g->M; ++m)
+      for (int c = 0; c < 256; ++c)
+        for (int w = 0; w < wps; ++w) {
+          uint32_t word = 0;
+          for (int b = 0; b < 4; ++b) {
+            const float v = g->codebook[((size_t)m * 256 + c) * ix->dsub + 4 * w + b];
+            word |= (uint32_t)(uint8_t)v << (8 * b);
+          }
+          words[((size_t)m * 256 + c) * wps + w] = word;
+        }
+    ANN_TRY(cudaMalloc(&ix->cb_words, words.size() * 4), "cudaMalloc codebook");
+    ANN_TRY(cudaMemcpy(ix->cb_words, words.data(), words.size() * 4, cudaMemcpyHostToDevice), "upload codebook");
+  } else {
+    const size_t vbytes = (size_t)n * d * elt_size(g->dtype);
+    ANN_TRY(cudaMalloc(&ix->vectors, vbytes), "cudaMalloc vectors");
+    ANN_TRY(cudaMemcpy(ix->vectors, g->vectors, vbytes, cudaMemcpyHostToDevice), "upload vectors");
+    ix->adj_stride = align_up(R, 4);
+    ix->block_bytes = ix->adj_stride * 4;
+    std::vector<int32_t> rows((size_t)n * ix->adj_stride, -1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int j = 0; j < R; ++j) {
+        const int32_t v = g->adj[(size_t)i * R + j];
+        if (v < 0) break;
+        rows[(size_t)i * ix->adj_stride + j] = v;
+      }
+    ANN_TRY(cudaMalloc(&ix->adj, rows.size() * 4), "cudaMalloc adjacency");
+    ANN_TRY(cudaMemcpy(ix->adj, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice), "upload adjacency");
+  }
+#undef ANN_TRY
+  *out = ix;
+  return ANN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int validate_search(const ann_index* ix, const void* q, int64_t nq, int k, int L, int depth,
+                    const void* ids, const void* dists) {
+  if (!ix) return set_error(ANN_EINVAL, "index is NULL");
+  if (nq < 0 || nq >= INT32_MAX) return set_error(ANN_EINVAL, "nq=%lld out of range", (long long)nq);
+  if (k < 1 || L < k || L > kMaxL) return set_error(ANN_EINVAL, "need 1 <= k <= L <= %d (k=%d, L=%d)", kMaxL, k, L);
+  if (k > 256) return set_error(ANN_EINVAL, "k=%d > 256", k);
+  if (depth < 0 || depth > kMaxDepth) return set_error(ANN_EINVAL, "depth=%d out of range [0,%d]", depth, kMaxDepth);
+  if (nq > 0 && (!q || !ids || !dists)) return set_error(ANN_EINVAL, "queries, ids and dists are required");
+  return ANN_OK;
+}
+
+// Enqueue one search of nq device-resident queries on `st`.
+int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int depth, int32_t* ids,
+                   float* dists, const ann_trace* tr, cudaStream_t st, bool timed) {
+  if (nq == 0) return ANN_OK;
+  const int slot_bytes = ix->block_bytes;
+  SearchPlan plan;
+  cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan);
+  if (e != cudaSuccess) return cuda_error(e, "plan search");
+  const size_t want = ((size_t)plan.blocks * plan.warps_per_block) << plan.vis_log2;
+  if (want > ix->vis_words) {
+    // tables must start all-zero; the kernel clears after each query
+    cudaError_t s = cudaStreamSynchronize(st);
+    if (s != cudaSuccess) return cuda_error(s, "sync before scratch growth");
+    cudaFree(ix->vis);
+    ix->vis = nullptr;
+    ix->vis_words = 0;
+    e = cudaMalloc(&ix->vis, want * 4);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc visited tables");
+    e = cudaMemset(ix->vis, 0, want * 4);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemset visited tables");
+    ix->vis_words = want;
+  }
+  SearchArgs a;
+  a.n = (int32_t)ix->n;
+  a.d = ix->d;
+  a.R = ix->R;
+  a.entry = ix->entry;
+  a.M = ix->M;
+  a.dsub = ix->dsub;
+  a.blocks = ix->blocks_dev;
+  a.block_bytes = ix->block_bytes;
+  a.ids_off = ix->ids_off;
+  a.deg_off = ix->deg_off;
+  a.codes = ix->codes;
+  a.cb_words = ix->cb_words;
+  a.vectors = ix->vectors;
+  a.adj = ix->adj;
+  a.adj_stride = ix->adj_stride;
+  a.queries = q;
+  a.nq = (int32_t)nq;
+  a.k = k;
+  a.L = L;
+  a.depth = depth;
+  a.ids = ids;
+  a.dists = dists;
+  a.steps = tr ? tr->steps : nullptr;
+  a.status = tr ? tr->status : nullptr;
+  a.t_begin = tr ? tr->t_begin : nullptr;
+  a.t_end = tr ? tr->t_end : nullptr;
+  a.vis = ix->vis;
+  a.vis_log2 = plan.vis_log2;
+  a.counters = ix->counters;
+  a.expansions = ix->expansions;
+  e = cudaMemsetAsync(ix->counters, 0, sizeof(int32_t), st);  // next-query counter
+  if (e != cudaSuccess) return cuda_error(e, "reset work counter");
+  if (timed) cudaEventRecord(ix->ev0, st);
+  e = launch_search(a, plan, st);
+  if (e != cudaSuccess) return cuda_error(e, "search kernel launch");
+  if (timed) cudaEventRecord(ix->ev1, st);
+  return ANN_OK;
+}
+
+// Read and reset the device-side failure counters and expansion total.
+int collect(ann_index* ix, cudaStream_t st, int64_t queries, ann_search_stats* stats, bool timed) {
+  int32_t c[4];
+  unsigned long long ex = 0;
+  cudaError_t e = cudaMemcpyAsync(c, ix->counters, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ex, ix->expansions, sizeof(ex), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "search");
+  const int32_t init[4] = {0, 0, INT32_MAX, 0};
+  e = cudaMemcpyAsync(ix->counters, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->expansions, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "reset counters");
+  float ms = 0.f;
+  if (timed) cudaEventElapsedTime(&ms, ix->ev0, ix->ev1);
+  if (stats) {
+    stats->queries = queries;
+    stats->expansions = (int64_t)ex;
+    stats->block_bytes = ix->block_bytes;
+    stats->n_failed = c[1];
+    stats->first_failed = c[1] > 0 ? c[2] : -1;
+    stats->kernel_ms = ms;
+  }
+  if (c[1] > 0)
+    return set_error(ANN_ENOMEM, "%d queries overflowed their visited set (first: query %d)", c[1], c[2]);
+  return ANN_OK;
+}
+
+struct BusyGuard {
+  ann_index* ix;
+  bool ok;
+  explicit BusyGuard(ann_index* i) : ix(i) {
+    int z = 0;
+    ok = ix->busy.compare_exchange_strong(z, 1);
+  }
+  ~BusyGuard() {
+    if (ok) ix->busy.store(0);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int ann_search(ann_index* ix, const void* queries, int64_t nq, int32_t k, int32_t L, int32_t depth,
+               int32_t* ids, float* dists, const ann_trace* trace, ann_search_stats* stats) {
+  int rc = validate_search(ix, queries, nq, k, L, depth, ids, dists);
+  if (rc != ANN_OK) return rc;
+  BusyGuard guard(ix);
+  if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (nq == 0) return ANN_OK;
+  cudaStream_t st = ix->stream;
+  const size_t qbytes = (size_t)nq * ix->d * elt_size(ix->dtype);
+  cudaError_t e = ix->q_stage.ensure(qbytes);
+  if (e == cudaSuccess) e = ix->ids_stage.ensure((size_t)nq * k * 4);
+  if (e == cudaSuccess) e = ix->dists_stage.ensure((size_t)nq * k * 4);
+  if (e == cudaSuccess && trace) {
+    e = ix->steps_stage.ensure((size_t)nq * 4);
+    if (e == cudaSuccess) e = ix->status_stage.ensure((size_t)nq * 4);
+    if (e == cudaSuccess) e = ix->tb_stage.ensure((size_t)nq * 8);
+    if (e == cudaSuccess) e = ix->te_stage.ensure((size_t)nq * 8);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "staging buffers");
+  e = cudaMemcpyAsync(ix->q_stage.p, queries, qbytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "copy queries");
+  ann_trace dtr{};
+  if (trace) {
+    dtr.steps = trace->steps ? static_cast<int32_t*>(ix->steps_stage.p) : nullptr;
+    dtr.status = trace->status ? static_cast<int32_t*>(ix->status_stage.p) : nullptr;
+    dtr.t_begin = trace->t_begin ? static_cast<int64_t*>(ix->tb_stage.p) : nullptr;
+    dtr.t_end = trace->t_end ? static_cast<int64_t*>(ix->te_stage.p) : nullptr;
+  }
+  int32_t* ids_d = static_cast<int32_t*>(ix->ids_stage.p);
+  float* dists_d = static_cast<float*>(ix->dists_stage.p);
+  rc = enqueue_search(ix, ix->q_stage.p, nq, k, L, depth, ids_d, dists_d, trace ? &dtr : nullptr,
+                      st, true);
+  if (rc != ANN_OK) return rc;
+  e = cudaMemcpyAsync(ids, ids_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dists, dists_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && trace) {
+    if (trace->steps) e = cudaMemcpyAsync(trace->steps, dtr.steps, nq * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && trace->status) e = cudaMemcpyAsync(trace->status, dtr.status, nq * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && trace->t_begin) e = cudaMemcpyAsync(trace->t_begin, dtr.t_begin, nq * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && trace->t_end) e = cudaMemcpyAsync(trace->t_end, dtr.t_end, nq * 8, cudaMemcpyDeviceToHost, st);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "copy results");
+  return collect(ix, st, nq, stats, true);
+}
+
+int ann_search_dev(ann_index* ix, const void* queries, int64_t nq, int32_t k, int32_t L, int32_t depth,
+                   int32_t* ids, float* dists, const ann_trace* trace, void* stream) {
+  int rc = validate_search(ix, queries, nq, k, L, depth, ids, dists);
+  if (rc != ANN_OK) return rc;
+  if (reinterpret_cast<uintptr_t>(queries) % 16)
+    return set_error(ANN_EINVAL, "queries must be 16-byte aligned");
+  BusyGuard guard(ix);
+  if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
+  rc = enqueue_search(ix, queries, nq, k, L, depth, ids, dists, trace,
+                      static_cast<cudaStream_t>(stream), false);
+  if (rc == ANN_OK) ix->pending_queries += nq;
+  return rc;
+}
+
+int ann_sync(ann_index* ix, void* stream, ann_search_stats* stats) {
+  if (!ix) return set_error(ANN_EINVAL, "index is NULL");
+  BusyGuard guard(ix);
+  if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int64_t q = ix->pending_queries;
+  ix->pending_queries = 0;
+  return collect(ix, static_cast<cudaStream_t>(stream), q, stats, false);
+}
+
+int ann_knn_exact(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
+                  int64_t nq, int32_t k, int32_t* ids, float* dists) {
+  if (!base || !queries || !ids || !dists) return set_error(ANN_EINVAL, "NULL buffer");
+  if (dtype != ANN_U8 && dtype != ANN_F32) return set_error(ANN_EINVAL, "unknown dtype");
+  if (n < 1 || nq < 0 || k < 1 || k > 128 || d < 4 || d % 4 || d > (dtype == ANN_U8 ? 512 : 256))
+    return set_error(ANN_EINVAL, "knn: bad sizes (n=%lld d=%d k=%d)", (long long)n, d, k);
+  if (nq == 0) return ANN_OK;
+  const size_t es = elt_size(dtype);
+  void *db = nullptr, *dq = nullptr;
+  int32_t* di = nullptr;
+  float* dd = nullptr;
+  cudaError_t e = cudaMalloc(&db, (size_t)n * d * es);
+  if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)nq * d * es);
+  if (e == cudaSuccess) e = cudaMalloc(&di, (size_t)nq * k * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dd, (size_t)nq * k * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(db, base, (size_t)n * d * es, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dq, queries, (size_t)nq * d * es, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = knn_exact_device(db, dtype, n, d, dq, nq, k, di, dd, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(ids, di, (size_t)nq * k * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(dists, dd, (size_t)nq * k * 4, cudaMemcpyDeviceToHost);
+  cudaFree(db);
+  cudaFree(dq);
+  cudaFree(di);
+  cudaFree(dd);
+  if (e != cudaSuccess) return cuda_error(e, "knn");
+  return ANN_OK;
+}
+
+int ann_probe_read_bandwidth(int64_t bytes, int32_t block_bytes, int32_t tier, int32_t iters,
+                             double* gbps_out) {
+  if (!gbps_out || bytes < block_bytes || block_bytes < 16 || block_bytes % 16 || block_bytes > 4096 ||
+      iters < 1 || (tier != ANN_TIER_HOST_PINNED && tier != ANN_TIER_HBM))
+    return set_error(ANN_EINVAL, "probe: bad arguments");
+  const int64_t nblocks = bytes / block_bytes;
+  uint8_t* host = nullptr;
+  uint8_t* dev = nullptr;
+  unsigned long long* sink = nullptr;
+  cudaError_t e;
+  if (tier == ANN_TIER_HOST_PINNED) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&host), (size_t)nblocks * block_bytes,
+                      cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) {
+      std::memset(host, 1, (size_t)nblocks * block_bytes);
+      e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev), host, 0);
+    }
+  } else {
+    e = cudaMalloc(&dev, (size_t)nblocks * block_bytes);
+    if (e == cudaSuccess) e = cudaMemset(dev, 1, (size_t)nblocks * block_bytes);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned long long));
+  float ms = 0.f;
+  int64_t moved = 0;
+  if (e == cudaSuccess) e = launch_read_probe(dev, nblocks, block_bytes, iters, sink, 0, &ms, &moved);
+  if (host) cudaFreeHost(host);
+  else cudaFree(dev);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_error(e, "probe");
+  *gbps_out = ms > 0.f ? (double)moved / (ms * 1e-3) / 1e9 : 0.0;
+  return ANN_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Index files: "ANNIDX01", int64 n, int32 d, dtype, R, entry, M, 0, then the
+// vectors, the adjacency, and (M > 0) the codebook and the codes.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FileHeader {
+  char magic[8];
+  int64_t n;
+  int32_t d, dtype, R, entry, M, zero;
+};
+
+bool write_all(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+bool read_all(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
+
+}  // namespace
+
+extern "C" {
+
+int ann_save_graph_file(const char* path, const ann_graph_desc* g) {
+  if (!path) return set_error(ANN_EINVAL, "path is NULL");
+  ann_graph_desc chk = *g;
+  chk.tier = ANN_TIER_HBM;
+  int rc = validate_desc(&chk);
+  if (rc != ANN_OK) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_error(ANN_EIO, "cannot open %s for writing", path);
+  FileHeader h;
+  std::memcpy(h.magic, "ANNIDX01", 8);
+  h.n = g->n;
+  h.d = g->d;
+  h.dtype = g->dtype;
+  h.R = g->R;
+  h.entry = g->entry;
+  h.M = g->M;
+  h.zero = 0;
+  bool ok = write_all(f, &h, sizeof(h)) &&
+            write_all(f, g->vectors, (size_t)g->n * g->d * elt_size(g->dtype)) &&
+            write_all(f, g->adj, (size_t)g->n * g->R * 4);
+  if (ok && g->M > 0)
+    ok = write_all(f, g->codebook, (size_t)g->M * 256 * (g->d / g->M) * 4) &&
+         write_all(f, g->codes, (size_t)g->n * g->M);
+  ok = (fclose(f) == 0) && ok;
+  return ok ? ANN_OK : set_error(ANN_EIO, "short write to %s", path);
+}
+
+int ann_load_graph_file(ann_index** out, const char* path, int32_t tier) {
+  if (!out || !path) return set_error(ANN_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_error(ANN_EIO, "cannot open %s", path);
+  FileHeader h;
+  if (!read_all(f, &h, sizeof(h)) || std::memcmp(h.magic, "ANNIDX01", 8) != 0) {
+    fclose(f);
+    return set_error(ANN_EIO, "%s is not an index file", path);
+  }
+  if (h.n < 1 || h.n >= INT32_MAX || h.d < 4 || h.d > kMaxD || h.R < 1 || h.R > kMaxR ||
+      h.M < 0 || h.M > kMaxM || (h.M > 0 && h.d % h.M) || (h.dtype != ANN_U8 && h.dtype != ANN_F32)) {
+    fclose(f);
+    return set_error(ANN_EIO, "%s: corrupt header", path);
+  }
+  std::vector<uint8_t> vec((size_t)h.n * h.d * elt_size(h.dtype));
+  std::vector<int32_t> adj((size_t)h.n * h.R);
+  std::vector<float> cb;
+  std::vector<uint8_t> codes;
+  bool ok = read_all(f, vec.data(), vec.size()) && read_all(f, adj.data(), adj.size() * 4);
+  if (ok && h.M > 0) {
+    cb.resize((size_t)h.M * 256 * (h.d / h.M));
+    codes.resize((size_t)h.n * h.M);
+    ok = read_all(f, cb.data(), cb.size() * 4) && read_all(f, codes.data(), codes.size());
+  }
+  fclose(f);
+  if (!ok) return set_error(ANN_EIO, "%s is truncated", path);
+  ann_graph_desc g;
+  g.n = h.n;
+  g.d = h.d;
+  g.dtype = h.dtype;
+  g.R = h.R;
+  g.entry = h.entry;
+  g.vectors = vec.data();
+  g.adj = adj.data();
+  g.M = h.M;
+  g.codebook = h.M > 0 ? cb.data() : nullptr;
+  g.codes = h.M > 0 ? codes.data() : nullptr;
+  g.tier = tier;
+  return ann_load_graph(out, &g);
+}
+
+}  // extern "C"

@@ -1,0 +1,634 @@
+// Persistent relaxed-pipeline graph search kernel for sm_103a.
+//
+// One warp runs one query at a time and takes the next query index from a
+// global counter when it finishes (persistent grid sized to the SMs'
+// residency).  Per query the warp:
+//   a1  builds the PQ lookup table of the query in its shared memory
+//       (T[m][c] = squared distance between query subvector m and centroid c,
+//       an exact integer from __vabsdiffu4 + __dp4a);
+//   a2  seeds the candidate list with the entry node;
+//   then loops over search steps (Section "Data-Dependency in Traditional
+//   Best-First Search": pop the closest candidate, read its node, compute
+//   its neighbours' distances, insert them):
+//   a3  select: first candidate not yet chosen for a fetch;
+//   a4  fetch: copy its node block (vector + degree + neighbour ids) from the
+//       storage tier (host pinned memory over PCIe, or HBM) into a ring slot
+//       in shared memory with per-lane 16-byte cp.async -- one group per
+//       fetch, owned by this warp alone (query-grained I/O, Section
+//       "Resource-Efficient Query-Grained Concurrent I/O Stack");
+//   a5  wait: only when more than `depth` fetches are in flight does the warp
+//       wait, and only for its own oldest fetch (cp.async.wait_group) -- so
+//       the node fetched at step i was chosen before the expansions of the
+//       previous `depth` steps were merged (Section "Dependency Relaxed
+//       Strategy"; depth 0 is the synchronous search);
+//   a6  exact distance of the expanded node into the sorted top-k results;
+//   a7  neighbour ids -> exact visited set (per-warp open-addressing table in
+//       global memory, atomicCAS inserts, cleared after each query);
+//   a8  PQ codes of the unseen neighbours gathered from HBM (16-byte loads)
+//       and their asymmetric distances summed from the lookup table;
+//   a9  warp bitonic sort of the new (distance, id) keys, merge-path merge
+//       into the candidate list, truncation to L;
+//   a10 stop when nothing is selectable and nothing is in flight;
+//   a11 write the k results.
+// The exact-navigation modes replace a1/a8 by exact distances of neighbour
+// vectors gathered from HBM, and fetch the node's adjacency row instead of a
+// node block; the result distance of an expanded node is its list distance.
+#include <cstdint>
+
+#include "ann_internal.h"
+
+namespace ann {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kNoKey = ~0ull;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Wait until at most n of this thread's cp.async groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+  }
+}
+
+__device__ __forceinline__ long long global_timer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Squared distance of 4 packed uint8 pairs, exact.
+__device__ __forceinline__ unsigned sq4(unsigned a, unsigned b, unsigned acc) {
+  unsigned t = __vabsdiffu4(a, b);
+  return __dp4a(t, t, acc);
+}
+
+__device__ __forceinline__ unsigned long long make_key(unsigned dist, unsigned id) {
+  return (static_cast<unsigned long long>(dist) << 32) | id;
+}
+
+// Ascending bitonic sort of 32*NB keys; element i = t*32 + lane lives in v[t].
+template <int NB>
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&v)[NB], int lane) {
+  constexpr int N = 32 * NB;
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 32) {
+        const int ts = stride >> 5;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if ((t & ts) == 0) {
+            const int t2 = t | ts;
+            const bool asc = (((t << 5) | lane) & size) == 0;
+            unsigned long long a = v[t], b = v[t2];
+            const bool swap = asc ? (a > b) : (a < b);
+            v[t] = swap ? b : a;
+            v[t2] = swap ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          const unsigned long long mine = v[t];
+          const unsigned long long other = __shfl_xor_sync(kFull, mine, stride);
+          const int i = (t << 5) | lane;
+          const bool asc = (i & size) == 0;
+          const bool lower = (lane & stride) == 0;
+          const bool take_min = (lower == asc);
+          v[t] = take_min ? (mine < other ? mine : other) : (mine < other ? other : mine);
+        }
+      }
+    }
+  }
+}
+
+// Number of entries of sorted a[0..len) that are < x.
+__device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int len,
+                                               unsigned long long x) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned hash_slot(unsigned id, int log2cap) {
+  return (id * 2654435761u) >> (32 - log2cap);
+}
+
+struct QueryState {
+  unsigned long long* cur_keys;
+  unsigned long long* nxt_keys;
+  unsigned char* cur_flags;
+  unsigned char* nxt_flags;
+  int len;
+  int nres;
+};
+
+// Insert key x into the ascending top-k result buffer res[0..nres).
+__device__ __forceinline__ void result_insert(unsigned long long* res, int& nres, int k,
+                                              unsigned long long x, int lane) {
+  if (nres == k && x >= res[k - 1]) return;  // res is read by every lane: uniform
+  int pos = 0;
+  for (int b = 0; b < nres; b += 32) {
+    const int j = b + lane;
+    pos += __popc(__ballot_sync(kFull, j < nres && res[j] < x));
+  }
+  const int last = nres < k ? nres : k - 1;  // entries [pos, last) move up by one
+  for (int b = ((last - 1) >> 5) << 5; b >= pos - 31 && b >= 0; b -= 32) {
+    const int j = b + lane;
+    unsigned long long val = 0;
+    const bool mv = j >= pos && j < last;
+    if (mv) val = res[j];
+    __syncwarp();
+    if (mv) res[j + 1] = val;
+    __syncwarp();
+  }
+  if (lane == 0) res[pos] = x;
+  __syncwarp();
+  nres = nres < k ? nres + 1 : k;
+}
+
+// Merge the sorted new candidates cand[0..c) into the list, keep L entries.
+// Entries before the rank of cand[0] keep their place (plain copy); only the
+// tail needs a rank lookup.  Returns the rank of cand[0] (the first position
+// whose entry changed), or L if nothing entered.
+__device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned long long* cand,
+                                                int c, int L, int lane) {
+  if (c == 0) return L;
+  if (s.len == L && cand[0] > s.cur_keys[L - 1]) return L;  // nothing would enter
+  const int pos0 = lower_bound_u64(s.cur_keys, s.len, cand[0]);
+  for (int i = lane; i < pos0; i += 32) {
+    s.nxt_keys[i] = s.cur_keys[i];
+    s.nxt_flags[i] = s.cur_flags[i];
+  }
+  for (int i = pos0 + lane; i < s.len; i += 32) {
+    const unsigned long long a = s.cur_keys[i];
+    const int p = i + lower_bound_u64(cand, c, a);
+    if (p < L) {
+      s.nxt_keys[p] = a;
+      s.nxt_flags[p] = s.cur_flags[i];
+    }
+  }
+  for (int j = lane; j < c; j += 32) {
+    const unsigned long long b = cand[j];
+    const int p = j + lower_bound_u64(s.cur_keys + pos0, s.len - pos0, b) + pos0;
+    if (p < L) {
+      s.nxt_keys[p] = b;
+      s.nxt_flags[p] = 0;
+    }
+  }
+  __syncwarp();
+  unsigned long long* tk = s.cur_keys;
+  s.cur_keys = s.nxt_keys;
+  s.nxt_keys = tk;
+  unsigned char* tf = s.cur_flags;
+  s.cur_flags = s.nxt_flags;
+  s.nxt_flags = tf;
+  s.len = (s.len + c < L) ? s.len + c : L;
+  return pos0;
+}
+
+// Exact squared distance between the query (in shared memory) and base vector w.
+template <int MODE>
+__device__ __forceinline__ unsigned exact_dist_warp(const SearchArgs& a, const unsigned char* qs,
+                                                    int w, int lane) {
+  if (MODE == kModeExactF32) {
+    const float4* x = reinterpret_cast<const float4*>(static_cast<const float*>(a.vectors) +
+                                                      static_cast<size_t>(w) * a.d);
+    const float4* q = reinterpret_cast<const float4*>(qs);
+    float acc = 0.f;
+    for (int j = lane; j < (a.d >> 2); j += 32) {
+      const float4 xv = __ldg(x + j), qv = q[j];
+      float t;
+      t = qv.x - xv.x; acc = fmaf(t, t, acc);
+      t = qv.y - xv.y; acc = fmaf(t, t, acc);
+      t = qv.z - xv.z; acc = fmaf(t, t, acc);
+      t = qv.w - xv.w; acc = fmaf(t, t, acc);
+    }
+    return __float_as_uint(warp_sum_f32(acc));
+  } else {
+    const unsigned* x = reinterpret_cast<const unsigned*>(static_cast<const uint8_t*>(a.vectors) +
+                                                          static_cast<size_t>(w) * a.d);
+    const unsigned* q = reinterpret_cast<const unsigned*>(qs);
+    unsigned acc = 0;
+    for (int j = lane; j < (a.d >> 2); j += 32) acc = sq4(q[j], __ldg(x + j), acc);
+    return warp_sum_u32(acc);
+  }
+}
+
+template <int MODE, int NB>
+__device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem& lay,
+                          uint32_t* vis, int qi, int lane) {
+  const long long t0 = global_timer_ns();
+  const int d = a.d, L = a.L, k = a.k, D = a.depth, n = a.n;
+  const int log2cap = a.vis_log2;
+  const unsigned cap_mask = (1u << log2cap) - 1u;
+  const int vis_limit = (3 << log2cap) >> 2;  // overflow above 3/4 load
+
+  unsigned* lut = reinterpret_cast<unsigned*>(ws + lay.lut);
+  unsigned char* ring = ws + lay.ring;
+  unsigned char* qs = ws + lay.q;
+  unsigned long long* res = reinterpret_cast<unsigned long long*>(ws + lay.res);
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(ws + lay.cand);
+  unsigned long long* ring_key = reinterpret_cast<unsigned long long*>(ws + lay.ring_key);
+  const int slot_bytes = (MODE == kModePqU8) ? a.block_bytes : a.adj_stride * 4;
+
+  QueryState s;
+  s.cur_keys = reinterpret_cast<unsigned long long*>(ws + lay.keys_a);
+  s.nxt_keys = reinterpret_cast<unsigned long long*>(ws + lay.keys_b);
+  s.cur_flags = ws + lay.flags_a;
+  s.nxt_flags = ws + lay.flags_b;
+
+  // ---- query vector into shared memory
+  {
+    const int qbytes = (MODE == kModeExactF32) ? d * 4 : d;
+    const unsigned* src = reinterpret_cast<const unsigned*>(
+        static_cast<const uint8_t*>(a.queries) + static_cast<size_t>(qi) * qbytes);
+    unsigned* dst = reinterpret_cast<unsigned*>(qs);
+    for (int j = lane; j < (qbytes >> 2); j += 32) dst[j] = __ldg(src + j);
+  }
+  __syncwarp();
+
+  // ---- a1: lookup table T[m][c], exact integers
+  if (MODE == kModePqU8) {
+    const int wps = a.dsub >> 2;  // 32-bit words per subvector
+    const unsigned* qw = reinterpret_cast<const unsigned*>(qs);
+    for (int m = 0; m < a.M; ++m) {
+      for (int c = lane; c < 256; c += 32) {
+        const unsigned* cw = a.cb_words + (static_cast<size_t>(m) * 256 + c) * wps;
+        unsigned acc = 0;
+        for (int w = 0; w < wps; ++w) acc = sq4(qw[m * wps + w], __ldg(cw + w), acc);
+        lut[m * 256 + c] = acc;
+      }
+    }
+    __syncwarp();
+  }
+
+  // ---- a2: entry node
+  unsigned entry_dist;
+  if (MODE == kModePqU8) {
+    const uint8_t* code = a.codes + static_cast<size_t>(a.entry) * a.M;
+    unsigned part = 0;
+    for (int m = lane; m < a.M; m += 32) part += lut[m * 256 + code[m]];
+    entry_dist = warp_sum_u32(part);
+  } else {
+    entry_dist = exact_dist_warp<MODE>(a, qs, a.entry, lane);
+  }
+  if (lane == 0) {
+    s.cur_keys[0] = make_key(entry_dist, a.entry);
+    s.cur_flags[0] = 0;
+    atomicCAS(vis + hash_slot(a.entry, log2cap), 0u, static_cast<unsigned>(a.entry) + 1u);
+  }
+  for (int j = lane; j < k; j += 32) res[j] = kNoKey;
+  __syncwarp();
+  s.len = 1;
+  s.nres = 0;
+  int head = 0, inflight = 0, steps = 0, visited = 1, status = ANN_OK;
+  int first_open = 0;  // every list entry before this position is selected
+  const int max_steps = n + 1;  // each node is expanded at most once
+
+  for (;;) {
+    // ---- a3: select the first candidate not chosen yet
+    int sel = -1;
+    for (int b = first_open; b < s.len; b += 32) {
+      const int i = b + lane;
+      const unsigned m = __ballot_sync(kFull, i < s.len && s.cur_flags[i] == 0);
+      if (m) {
+        sel = b + __ffs(m) - 1;
+        break;
+      }
+    }
+    first_open = sel >= 0 ? sel + 1 : s.len;
+    if (sel >= 0) {
+      // ---- a4: issue the fetch of its block into the next ring slot
+      const unsigned long long key = s.cur_keys[sel];
+      const unsigned v = static_cast<unsigned>(key);
+      int slot = head + inflight;
+      if (slot > D) slot -= D + 1;
+      __syncwarp();
+      if (lane == 0) {
+        s.cur_flags[sel] = 1;
+        ring_key[slot] = key;
+      }
+      const uint8_t* src = (MODE == kModePqU8)
+                               ? a.blocks + static_cast<size_t>(v) * a.block_bytes
+                               : reinterpret_cast<const uint8_t*>(
+                                     a.adj + static_cast<size_t>(v) * a.adj_stride);
+      unsigned char* dst = ring + slot * slot_bytes;
+      for (int off = lane * 16; off < slot_bytes; off += 512) cp_async_16(dst + off, src + off);
+      cp_async_commit();
+      ++inflight;
+      __syncwarp();  // lane 0's flag and ring_key writes are seen by every lane
+    }
+    if (inflight > D || (sel < 0 && inflight > 0)) {
+      // ---- a5: wait for this warp's oldest fetch only
+      cp_async_wait_pending(inflight - 1);
+      __syncwarp();
+      const unsigned char* blk = ring + head * slot_bytes;
+      const unsigned long long ukey = ring_key[head];
+      const unsigned u = static_cast<unsigned>(ukey);
+      head = (head == D) ? 0 : head + 1;
+      --inflight;
+      ++steps;
+
+      // ---- a6: exact distance of u into the results
+      unsigned long long rkey;
+      if (MODE == kModePqU8) {
+        const unsigned* xw = reinterpret_cast<const unsigned*>(blk);
+        const unsigned* qw = reinterpret_cast<const unsigned*>(qs);
+        unsigned acc = 0;
+        for (int j = lane; j < (d >> 2); j += 32) acc = sq4(qw[j], xw[j], acc);
+        rkey = make_key(warp_sum_u32(acc), u);
+      } else {
+        rkey = ukey;  // exact navigation: the list distance is the exact distance
+      }
+      result_insert(res, s.nres, k, rkey, lane);
+
+      // ---- a7: neighbour ids and the visited set
+      int deg;
+      const int32_t* nbr;
+      if (MODE == kModePqU8) {
+        deg = static_cast<int>(*reinterpret_cast<const unsigned*>(blk + a.deg_off));
+        deg = deg < a.R ? deg : a.R;
+        nbr = reinterpret_cast<const int32_t*>(blk + a.ids_off);
+      } else {
+        deg = a.R;
+        nbr = reinterpret_cast<const int32_t*>(blk);
+      }
+      int w[NB];
+      unsigned pos[NB];
+      bool pending[NB], fresh[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int j = t * 32 + lane;
+        int id = j < deg ? nbr[j] : -1;
+        if (id >= n) id = -1;  // validated at load; never trusted blindly
+        w[t] = id;
+        pending[t] = id >= 0;
+        fresh[t] = false;
+        pos[t] = pending[t] ? hash_slot(static_cast<unsigned>(id), log2cap) : 0u;
+      }
+      // PQ codes of every listed neighbour, issued before the visited probes
+      // so that both round trips overlap.
+      uint4 code[NB][kMaxM / 16];
+      if (MODE == kModePqU8) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if (w[t] >= 0) {
+            const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
+#pragma unroll
+            for (int c = 0; c < kMaxM / 16; ++c)
+              if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
+          }
+        }
+      }
+      for (int probe = 0; probe <= static_cast<int>(cap_mask); ++probe) {
+        bool any = false;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if (pending[t]) {
+            const unsigned want = static_cast<unsigned>(w[t]) + 1u;
+            const unsigned old = atomicCAS(vis + pos[t], 0u, want);
+            if (old == 0u) {
+              fresh[t] = true;
+              pending[t] = false;
+            } else if (old == want) {
+              pending[t] = false;
+            } else {
+              pos[t] = (pos[t] + 1u) & cap_mask;
+              any = true;
+            }
+          }
+        }
+        if (!__any_sync(kFull, any)) break;
+      }
+      int nfresh = 0;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) nfresh += __popc(__ballot_sync(kFull, fresh[t]));
+      visited += nfresh;
+
+      // ---- a8: navigation distances of the unseen neighbours
+      unsigned long long key[NB];
+      if (MODE == kModePqU8) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          key[t] = kNoKey;
+          if (fresh[t]) {
+            unsigned dist = 0;
+#pragma unroll
+            for (int c = 0; c < kMaxM / 16; ++c) {
+              if (c < (a.M >> 4)) {
+                const unsigned wd[4] = {code[t][c].x, code[t][c].y, code[t][c].z, code[t][c].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int m0 = c * 16 + e * 4;
+                  dist += lut[(m0 + 0) * 256 + (wd[e] & 0xff)];
+                  dist += lut[(m0 + 1) * 256 + ((wd[e] >> 8) & 0xff)];
+                  dist += lut[(m0 + 2) * 256 + ((wd[e] >> 16) & 0xff)];
+                  dist += lut[(m0 + 3) * 256 + (wd[e] >> 24)];
+                }
+              }
+            }
+            key[t] = make_key(dist, static_cast<unsigned>(w[t]));
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          key[t] = kNoKey;
+          unsigned m = __ballot_sync(kFull, fresh[t]);
+          while (m) {
+            const int src_lane = __ffs(m) - 1;
+            m &= m - 1;
+            const int id = __shfl_sync(kFull, w[t], src_lane);
+            const unsigned dist = exact_dist_warp<MODE>(a, qs, id, lane);
+            if (lane == src_lane) key[t] = make_key(dist, static_cast<unsigned>(id));
+          }
+        }
+      }
+
+      // ---- a9: sort the new keys, merge into the list, truncate to L
+      if (nfresh > 0) {
+        warp_bitonic_sort<NB>(key, lane);
+#pragma unroll
+        for (int t = 0; t < NB; ++t) cand[t * 32 + lane] = key[t];
+        __syncwarp();
+        const int changed = merge_candidates(s, cand, nfresh, L, lane);
+        if (changed < first_open) first_open = changed;
+      }
+      __syncwarp();
+
+      if (visited > vis_limit || steps >= max_steps) {
+        status = ANN_ENOMEM;
+        break;
+      }
+    } else if (sel < 0) {
+      break;  // ---- a10: nothing selectable, nothing in flight
+    }
+  }
+  // Drain fetches still in flight after an early stop (none on normal exit).
+  cp_async_wait_pending(0);
+  __syncwarp();
+
+  // ---- a11: results
+  for (int j = lane; j < k; j += 32) {
+    const unsigned long long r = j < s.nres ? res[j] : kNoKey;
+    const bool ok = r != kNoKey;
+    a.ids[static_cast<size_t>(qi) * k + j] = ok ? static_cast<int32_t>(r & 0xffffffffu) : -1;
+    const unsigned dbits = static_cast<unsigned>(r >> 32);
+    a.dists[static_cast<size_t>(qi) * k + j] =
+        ok ? ((MODE == kModeExactF32) ? __uint_as_float(dbits) : static_cast<float>(dbits))
+           : __int_as_float(0x7f800000);
+  }
+  // Clear the visited table for the next query of this warp.
+  {
+    uint4* t4 = reinterpret_cast<uint4*>(vis);
+    const int n4 = (1 << log2cap) >> 2;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int j = lane; j < n4; j += 32) t4[j] = z;
+  }
+  if (lane == 0) {
+    if (a.steps) a.steps[qi] = steps;
+    if (a.status) a.status[qi] = status;
+    if (a.t_begin) a.t_begin[qi] = t0;
+    if (a.t_end) a.t_end[qi] = global_timer_ns();
+    atomicAdd(a.expansions, static_cast<unsigned long long>(steps));
+    if (status != ANN_OK) {
+      atomicAdd(&a.counters[1], 1);
+      atomicMin(&a.counters[2], qi);
+    }
+  }
+  __syncwarp();
+}
+
+template <int MODE, int NB>
+__global__ void search_kernel(SearchArgs a, int smem_per_warp, int slot_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  unsigned char* ws = smem + wib * smem_per_warp;
+  const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, slot_bytes, a.depth, a.L, a.k, NB);
+  const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
+  uint32_t* vis = a.vis + (gw << a.vis_log2);
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(&a.counters[0], 1);
+    qi = __shfl_sync(kFull, qi, 0);
+    if (qi >= a.nq) break;
+    run_query<MODE, NB>(a, ws, lay, vis, qi, lane);
+  }
+}
+
+template <int MODE, int NB>
+cudaError_t launch_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) {
+  const int smem = p.smem_per_warp * p.warps_per_block;
+  const int slot_bytes = (MODE == kModePqU8) ? a.block_bytes : a.adj_stride * 4;
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  search_kernel<MODE, NB><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, p.smem_per_warp,
+                                                                          slot_bytes);
+  return cudaGetLastError();
+}
+
+template <int MODE, int NB>
+cudaError_t occupancy_t(int smem_block, int threads, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<MODE, NB>,
+                                                       threads, smem_block);
+}
+
+using LaunchFn = cudaError_t (*)(const SearchArgs&, const SearchPlan&, cudaStream_t);
+using OccFn = cudaError_t (*)(int, int, int*);
+
+int nb_index(int nb) { return nb == 1 ? 0 : (nb == 2 ? 1 : 2); }
+
+LaunchFn launch_table(int mode, int nb) {
+  static const LaunchFn t[3][3] = {
+      {launch_t<kModePqU8, 1>, launch_t<kModePqU8, 2>, launch_t<kModePqU8, 4>},
+      {launch_t<kModeExactU8, 1>, launch_t<kModeExactU8, 2>, launch_t<kModeExactU8, 4>},
+      {launch_t<kModeExactF32, 1>, launch_t<kModeExactF32, 2>, launch_t<kModeExactF32, 4>}};
+  return t[mode][nb_index(nb)];
+}
+
+OccFn occ_table(int mode, int nb) {
+  static const OccFn t[3][3] = {
+      {occupancy_t<kModePqU8, 1>, occupancy_t<kModePqU8, 2>, occupancy_t<kModePqU8, 4>},
+      {occupancy_t<kModeExactU8, 1>, occupancy_t<kModeExactU8, 2>, occupancy_t<kModeExactU8, 4>},
+      {occupancy_t<kModeExactF32, 1>, occupancy_t<kModeExactF32, 2>, occupancy_t<kModeExactF32, 4>}};
+  return t[mode][nb_index(nb)];
+}
+
+}  // namespace
+
+cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
+                        int64_t nq, SearchPlan* plan) {
+  SearchPlan p;
+  p.mode = mode;
+  p.nb = R <= 32 ? 1 : (R <= 64 ? 2 : 4);
+  const WarpSmem lay = warp_smem_layout(mode, M, d, slot_bytes, depth, L, k, p.nb);
+  p.smem_per_warp = lay.total;
+  p.warps_per_block = 1;
+  // Visited table: next_pow2(2*R*(L+64)) slots (at least 4096), so a query
+  // may visit ~1.5*R*(L+64) nodes before it reports an overflow.
+  const int64_t want = 2ll * R * (L + 64);
+  int lg = 12;
+  while ((1ll << lg) < want && lg < 22) ++lg;
+  p.vis_log2 = lg;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = occ_table(mode, p.nb)(p.smem_per_warp * p.warps_per_block, 32 * p.warps_per_block, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t blocks = static_cast<int64_t>(sms) * per_sm;
+  const int64_t need = (nq + p.warps_per_block - 1) / p.warps_per_block;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  p.blocks = static_cast<int>(blocks);
+  *plan = p;
+  return cudaSuccess;
+}
+
+cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
+  return launch_table(plan.mode, plan.nb)(a, plan, stream);
+}
+
+}  // namespace ann

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA search kernel against the CPU oracle, element by element,
+on the same seeded inputs (graphs and PQ codebooks built by the oracle).
+
+uint8 data is exact on both sides, so ids, distances and per-query step counts
+must be identical.  float32 data: distances within 1e-5 relative, ids may
+differ only where the distance gap is below that, recall@10 within 0.002.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2507_10070_b300 as ann
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def u8_pq():
+    """SIFT-like uint8 index, 20,000 nodes, R=64, PQ M=32: oracle-built."""
+    mx = datagen.sift_like()
+    n, nq = 20_000, 333                        # nq: a ragged tail over the grid
+    base, q = mx.base(n), mx.queries(nq)
+    cb = oracle.pq_train(base[:5000], 32, datagen.kmeanspp_uniforms(mx.seed, 32), iters=8)
+    codes = oracle.pq_encode(base, cb)
+    entry = oracle.medoid(base)
+    adj = oracle.vamana(base, 64, 1.2, 96, entry, datagen.build_order(mx.seed, n),
+                        datagen.random_out_neighbours(mx.seed, n, 64))
+    return dict(base=base, q=q, cb=cb, codes=codes, entry=entry, adj=adj)
+
+
+@pytest.fixture(scope="module")
+def pq_index(u8_pq):
+    w = u8_pq
+    ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],
+                   tier=ann.ANN_TIER_HOST_PINNED)
+    yield ix
+    ix.close()
+
+
+def _oracle_pq(w, k, L, depth, q=None):
+    return oracle.search(w["base"], w["adj"], w["entry"], w["q"] if q is None else q, k, L, depth,
+                         codebook=w["cb"], codes=w["codes"])
+
+
+@pytest.mark.parametrize("L", [16, 64, 256])
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_pq_search_bit_exact(u8_pq, pq_index, L, depth):
+    k = 10
+    ids, dists, stats, tr = pq_index.search(u8_pq["q"], k, L, depth, trace=True)
+    oi, od, osteps = _oracle_pq(u8_pq, k, L, depth)
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], osteps)
+    assert np.all(tr["status"] == 0) and stats.n_failed == 0
+    assert stats.expansions == int(osteps.sum())
+
+
+@pytest.mark.parametrize("k,L", [(1, 1), (1, 8), (33, 40), (100, 128), (256, 512), (10, 1536)])
+def test_pq_search_k_and_L_extremes(u8_pq, pq_index, k, L):
+    ids, dists, _ = pq_index.search(u8_pq["q"][:97], k, L, 1)
+    oi, od, _ = _oracle_pq(u8_pq, k, L, 1, q=u8_pq["q"][:97])
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(dists.astype(np.float64), od)
+
+
+def test_pq_hbm_tier_matches_host_tier(u8_pq, pq_index):
+    w = u8_pq
+    ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"], tier=ann.ANN_TIER_HBM)
+    try:
+        a = ix.search(w["q"], 10, 64, 1)
+        b = pq_index.search(w["q"], 10, 64, 1)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    finally:
+        ix.close()
+
+
+def test_exact_u8_navigation_bit_exact(u8_pq):
+    w = u8_pq
+    ix = ann.Index(w["base"], w["adj"], w["entry"], tier=ann.ANN_TIER_HBM)
+    try:
+        for depth in (0, 1, 4):
+            ids, dists, _, tr = ix.search(w["q"], 10, 48, depth, trace=True)
+            oi, od, os_ = oracle.search(w["base"], w["adj"], w["entry"], w["q"], 10, 48, depth)
+            assert np.array_equal(ids, oi)
+            assert np.array_equal(dists.astype(np.float64), od)
+            assert np.array_equal(tr["steps"], os_)
+    finally:
+        ix.close()
+
+
+@pytest.fixture(scope="module")
+def f32_inmem():
+    """In-memory float workload: 10k float32 vectors, d=128, 32 clusters, 200
+    queries, Vamana R=32 alpha=1.2 L_build=64 built by the oracle."""
+    mx = datagen.inmemory_f32()
+    base, q = mx.base(10_000), mx.queries(200)
+    entry = oracle.medoid(base)
+    adj = oracle.vamana(base, 32, 1.2, 64, entry, datagen.build_order(mx.seed, 10_000),
+                        datagen.random_out_neighbours(mx.seed, 10_000, 32))
+    gi, gd = oracle.knn(base, q, 10)
+    return dict(base=base, q=q, entry=entry, adj=adj, gi=gi, gd=gd)
+
+
+def _check_f32(ids, dists, oi, od):
+    # distances agree within REL where the ids agree ...
+    same = ids == oi
+    assert np.all(np.abs(dists[same] - od[same]) <= REL * np.maximum(od[same], 1e-30))
+    # ... and a differing id is only a near-tie swap at that rank
+    diff = ~same
+    if diff.any():
+        assert np.all(np.abs(dists[diff] - od[diff]) <= REL * od[diff])
+    return float(same.mean())
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_exact_f32_inmemory_parity(f32_inmem, depth):
+    w = f32_inmem
+    ix = ann.Index(w["base"], w["adj"], w["entry"], tier=ann.ANN_TIER_HBM)
+    try:
+        ids, dists, _ = ix.search(w["q"], 10, 64, depth)
+        oi, od, _ = oracle.search(w["base"], w["adj"], w["entry"], w["q"], 10, 64, depth)
+        _check_f32(ids, dists, oi, od)
+        r_gpu = ann.recall_at_k(ids, w["gi"], w["gd"], dists)
+        r_orc = oracle.recall_at_k(oi, w["gi"], w["gd"], od)
+        assert abs(r_gpu - r_orc) <= 0.002
+        if depth == 0:
+            assert r_gpu >= 0.95
+    finally:
+        ix.close()
+
+
+def test_search_dev_matches_host_and_sync_reports(u8_pq, pq_index):
+    import torch
+    q = torch.from_numpy(u8_pq["q"]).cuda()
+    nq, k = q.shape[0], 10
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    steps = torch.empty(nq, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for _ in range(2):   # two calls before one sync accumulate
+            pq_index.search_dev(q, k, 64, 1, ids, dists, stream=st, trace={"steps": steps})
+    stats = pq_index.sync(st)
+    hi, hd, _, tr = pq_index.search(u8_pq["q"], k, 64, 1, trace=True)
+    assert np.array_equal(ids.cpu().numpy(), hi)
+    assert np.array_equal(dists.cpu().numpy(), hd)
+    assert np.array_equal(steps.cpu().numpy(), tr["steps"])
+    assert stats.queries == 2 * nq and stats.expansions == 2 * int(tr["steps"].sum())
+    assert stats.n_failed == 0 and stats.first_failed == -1
+    # timestamps: every query has a begin <= end
+    assert np.all(tr["t_end"] >= tr["t_begin"]) and np.all(tr["t_begin"] > 0)
+
+
+def test_edge_cases(u8_pq, pq_index):
+    # empty batch
+    ids, dists, stats = pq_index.search(u8_pq["q"][:0], 10, 32, 1)
+    assert ids.shape == (0, 10) and stats.queries == 0
+    # single query, deepest pipeline
+    ids, dists, _ = pq_index.search(u8_pq["q"][:1], 5, 5, 4)
+    oi, od, _ = _oracle_pq(u8_pq, 5, 5, 4, q=u8_pq["q"][:1])
+    assert np.array_equal(ids, oi)
+    # argument errors
+    for k, L, depth in [(0, 10, 0), (11, 10, 0), (10, 4097, 0), (10, 32, 5), (10, 32, -1)]:
+        with pytest.raises(ann.AnnError):
+            pq_index.search(u8_pq["q"][:4], k, L, depth)
+
+
+def test_degenerate_graphs():
+    # a single node, and an entry with no out-edges: results are padded
+    base = np.array([[1, 2, 3, 4], [9, 9, 9, 9]], np.uint8)
+    adj = np.array([[-1], [0]], np.int32)
+    ix = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
+    try:
+        ids, dists, _ = ix.search(np.array([[9, 9, 9, 9]], np.uint8), 2, 4, 2)
+        assert ids.tolist() == [[0, -1]]
+        assert dists[0, 0] == 8 * 8 + 7 * 7 + 6 * 6 + 5 * 5 and np.isinf(dists[0, 1])
+    finally:
+        ix.close()
+    one = ann.Index(base[:1], np.array([[-1]], np.int32), 0, tier=ann.ANN_TIER_HBM)
+    try:
+        ids, dists, _ = one.search(base[:1], 1, 1, 0)
+        assert ids.tolist() == [[0]] and dists[0, 0] == 0
+    finally:
+        one.close()
+
+
+def test_visited_overflow_reports_enomem():
+    """Host-side check of the device's failure path: a random graph of degree
+    128 and a list of 32 visits far more nodes than the visited table holds
+    (capacity 2*L*R slots, overflow above 3/4); the query must report
+    ANN_ENOMEM rather than diverge."""
+    rng = np.random.default_rng(5)
+    n, R = 60_000, 128
+    base = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    # random out-neighbours, never the node itself (a repeated id in a row is
+    # simply seen as visited the second time)
+    adj = ((np.arange(n)[:, None] + 1 + rng.integers(0, n - 1, size=(n, R))) % n).astype(np.int32)
+    ix = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
+    try:
+        q = rng.integers(0, 256, size=(3, 16)).astype(np.uint8)
+        ids, dists, stats, tr = ix.search(q, 10, 32, 1, trace=True)
+        assert np.all(tr["status"] == ann._abi.ANN_ENOMEM)
+        assert stats.n_failed == 3 and stats.first_failed == 0
+        with pytest.raises(ann.AnnError) as e:
+            ix.search(q, 10, 32, 1)
+        assert e.value.status == ann._abi.ANN_ENOMEM
+        # the tables were cleared after the failed queries: a repeat behaves the same
+        ids2, dists2, stats2, tr2 = ix.search(q, 10, 32, 1, trace=True)
+        assert np.array_equal(ids2, ids) and np.array_equal(tr2["steps"], tr["steps"])
+    finally:
+        ix.close()
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_knn_exact_matches_oracle(dtype):
+    mx = datagen.sift_like() if dtype == "u8" else datagen.inmemory_f32()
+    base, q = mx.base(7000), mx.queries(150)
+    ids, d = ann.knn_exact(base, q, 10)
+    oi, od = oracle.knn(base, q, 10)
+    if dtype == "u8":
+        assert np.array_equal(ids, oi) and np.array_equal(d.astype(np.float64), od)
+    else:
+        _check_f32(ids, d, oi, od)
+
+
+def test_read_probe_runs():
+    g_host = ann.probe_read_bandwidth(64 << 20, 512, ann.ANN_TIER_HOST_PINNED, 16)
+    g_hbm = ann.probe_read_bandwidth(256 << 20, 512, ann.ANN_TIER_HBM, 16)
+    assert g_host > 1.0 and g_hbm > g_host

@@ -70,9 +70,14 @@ def test_medoid_matches_numpy():
 
 
 def test_recall_tie_aware():
+    gi = np.array([[0, 1, 2]])
     gt = np.array([[1.0, 2.0, 2.0]])
-    assert oracle.recall_at_k(np.array([[0, 5, 2]]), gt, np.array([[1.0, 2.0, 2.0]]), 3) == 1.0
-    assert oracle.recall_at_k(np.array([[0, 5, -1]]), gt, np.array([[1.0, 2.0, np.inf]]), 3) == 2 / 3
+    # id 5 ties with the 3rd neighbour: it counts
+    assert oracle.recall_at_k(np.array([[0, 5, 2]]), gi, gt, np.array([[1.0, 2.0, 2.0]]), 3) == 1.0
+    assert oracle.recall_at_k(np.array([[0, 5, -1]]), gi, gt, np.array([[1.0, 2.0, np.inf]]), 3) == 2 / 3
+    # a true neighbour counts even if its reported distance rounds above the k-th
+    assert oracle.recall_at_k(np.array([[2, 1, 0]]), gi, gt, np.array([[1.0, 2.0000001, 2.0000001]]), 3) == 1.0
+    assert oracle.recall_at_k(np.array([[7, 8, 0]]), gi, gt, np.array([[2.5, 3.0, 1.0]]), 3) == 1 / 3
 
 
 # --------------------------------------------------------------------------
@@ -238,7 +243,7 @@ def test_search_invariants(small_f32):
                 assert set(ids[i].tolist()) <= set(exp.tolist())      # results come from expansions
             if depth == 0:
                 s0 = steps
-                recalls.append(oracle.recall_at_k(ids, gd, d))
+                recalls.append(oracle.recall_at_k(ids, gi, gd, d))
             else:
                 # Step bound of the convergence analysis (Eq. 5): |P_relax| <= (k+1) T.
                 # Its proof is informal and it does not hold for every query (one
@@ -264,7 +269,7 @@ def test_inmemory_workload_recall():
     gi, gd = oracle.knn(base, q, 10)
     ids0, d0, s0 = oracle.search(base, adj, med, q, 10, 64, 0)
     ids1, d1, s1 = oracle.search(base, adj, med, q, 10, 64, 1)
-    r0, r1 = oracle.recall_at_k(ids0, gd, d0), oracle.recall_at_k(ids1, gd, d1)
+    r0, r1 = oracle.recall_at_k(ids0, gi, gd, d0), oracle.recall_at_k(ids1, gi, gd, d1)
     assert r0 >= 0.95 and abs(r1 - r0) <= 0.01
     assert 1.0 <= s1.mean() / s0.mean() <= 1.10
     assert _bfs_reach(adj, med) >= 9990
