@@ -49,6 +49,8 @@ struct SearchArgs {
   // scratch
   uint32_t* vis;            // per-warp open-addressing visited tables, all zero between queries
   int32_t vis_log2;         // log2 of the table capacity per warp
+  uint32_t* vis_log;        // per-warp log of the table slots a query used (to clear them)
+  int32_t vis_log_cap;      // entries per warp in vis_log
   int32_t* counters;        // [0] next query, [1] failed queries, [2] first failed query
   unsigned long long* expansions;  // running total of expansions
 };
@@ -61,11 +63,12 @@ struct SearchPlan {
   int warps_per_block;
   int blocks;          // grid size (persistent)
   int vis_log2;
+  int vis_log_cap;
 };
 
 // Per-warp shared-memory layout (byte offsets), identical on host and device.
 struct WarpSmem {
-  int lut, ring, q, keys_a, keys_b, flags_a, flags_b, res, cand, ring_key, total;
+  int lut, ring, q, keys, flags, res, cand, rank, ring_key, total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -83,9 +86,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
   s.q = off;
   off += (mode == kModeExactF32) ? d * 4 : d;
   off = align_up(off, 16);
-  s.keys_a = off;
-  off += L * 8;
-  s.keys_b = off;
+  s.keys = off;
   off += L * 8;
   s.res = off;
   off += k * 8;
@@ -93,9 +94,9 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
   off += 32 * nb * 8;
   s.ring_key = off;
   off += (depth + 1) * 8;
-  s.flags_a = off;
-  off += align_up(L, 16);
-  s.flags_b = off;
+  s.rank = off;
+  off += 32 * nb * 4;
+  s.flags = off;
   off += align_up(L, 16);
   s.total = align_up(off, 128);
   return s;

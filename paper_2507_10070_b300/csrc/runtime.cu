@@ -76,6 +76,7 @@ struct ann_index {
   // scratch
   uint32_t* vis = nullptr;
   size_t vis_words = 0;
+  DevBuf vis_log;
   int32_t* counters = nullptr;              // device [4]
   unsigned long long* expansions = nullptr; // device [1]
   int64_t pending_queries = 0;              // ann_search_dev calls since ann_sync
@@ -102,7 +103,7 @@ void release(ann_index* ix) {
   cudaFree(ix->counters);
   cudaFree(ix->expansions);
   for (DevBuf* b : {&ix->q_stage, &ix->ids_stage, &ix->dists_stage, &ix->steps_stage,
-                    &ix->status_stage, &ix->tb_stage, &ix->te_stage})
+                    &ix->status_stage, &ix->tb_stage, &ix->te_stage, &ix->vis_log})
     b->release();
   if (ix->ev0) cudaEventDestroy(ix->ev0);
   if (ix->ev1) cudaEventDestroy(ix->ev1);
@@ -303,6 +304,13 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
     if (e != cudaSuccess) return cuda_error(e, "cudaMemset visited tables");
     ix->vis_words = want;
   }
+  const size_t log_bytes = (size_t)plan.blocks * plan.warps_per_block * plan.vis_log_cap * 4;
+  if (log_bytes > ix->vis_log.cap) {
+    cudaError_t s = cudaStreamSynchronize(st);
+    if (s != cudaSuccess) return cuda_error(s, "sync before scratch growth");
+    e = ix->vis_log.ensure(log_bytes);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc visited log");
+  }
   SearchArgs a;
   a.n = (int32_t)ix->n;
   a.d = ix->d;
@@ -332,6 +340,8 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   a.t_end = tr ? tr->t_end : nullptr;
   a.vis = ix->vis;
   a.vis_log2 = plan.vis_log2;
+  a.vis_log = static_cast<uint32_t*>(ix->vis_log.p);
+  a.vis_log_cap = plan.vis_log_cap;
   a.counters = ix->counters;
   a.expansions = ix->expansions;
   e = cudaMemsetAsync(ix->counters, 0, sizeof(int32_t), st);  // next-query counter

@@ -149,10 +149,9 @@ __device__ __forceinline__ unsigned hash_slot(unsigned id, int log2cap) {
 }
 
 struct QueryState {
-  unsigned long long* cur_keys;
-  unsigned long long* nxt_keys;
-  unsigned char* cur_flags;
-  unsigned char* nxt_flags;
+  unsigned long long* keys;  // candidate list, ascending (nav distance, id)
+  unsigned char* flags;      // 1 = chosen for a fetch already
+  int* rank;                 // scratch: list rank of each new candidate
   int len;
   int nres;
 };
@@ -181,42 +180,55 @@ __device__ __forceinline__ void result_insert(unsigned long long* res, int& nres
   nres = nres < k ? nres + 1 : k;
 }
 
-// Merge the sorted new candidates cand[0..c) into the list, keep L entries.
-// Entries before the rank of cand[0] keep their place (plain copy); only the
-// tail needs a rank lookup.  Returns the rank of cand[0] (the first position
+// Merge the sorted new candidates cand[0..c) into the list in place and keep
+// L entries.  rank_j = number of list entries below cand[j]; list entry i moves
+// to i + #{j : rank_j <= i} and cand[j] to j + rank_j.  Entries only move
+// right, so sweeping the tail in 32-entry chunks from the top down never
+// overwrites an entry not yet read; the candidates then fill the holes.
+// Entries before rank_0 keep their place.  Returns rank_0 (the first position
 // whose entry changed), or L if nothing entered.
 __device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned long long* cand,
                                                 int c, int L, int lane) {
   if (c == 0) return L;
-  if (s.len == L && cand[0] > s.cur_keys[L - 1]) return L;  // nothing would enter
-  const int pos0 = lower_bound_u64(s.cur_keys, s.len, cand[0]);
-  for (int i = lane; i < pos0; i += 32) {
-    s.nxt_keys[i] = s.cur_keys[i];
-    s.nxt_flags[i] = s.cur_flags[i];
-  }
-  for (int i = pos0 + lane; i < s.len; i += 32) {
-    const unsigned long long a = s.cur_keys[i];
-    const int p = i + lower_bound_u64(cand, c, a);
-    if (p < L) {
-      s.nxt_keys[p] = a;
-      s.nxt_flags[p] = s.cur_flags[i];
+  if (s.len == L && cand[0] > s.keys[L - 1]) return L;  // nothing would enter
+  for (int j = lane; j < c; j += 32) s.rank[j] = lower_bound_u64(s.keys, s.len, cand[j]);
+  __syncwarp();
+  const int pos0 = s.rank[0];
+  // p = #{j : rank_j <= top of the current chunk}
+  int p = c;
+  const int top_chunk = ((s.len - 1) >> 5) << 5;
+  while (p > 0 && s.rank[p - 1] > top_chunk + 31) --p;
+  for (int b = top_chunk; b >= (pos0 & ~31); b -= 32) {
+    const int i = b + lane;
+    const bool live = i >= pos0 && i < s.len;
+    unsigned long long key = 0;
+    unsigned char flag = 0;
+    if (live) {
+      key = s.keys[i];
+      flag = s.flags[i];
     }
+    // r(i) = p - #{j : i < rank_j <= b + 31}; walk the ranks inside this chunk
+    int r = p;
+    while (p > 0 && s.rank[p - 1] >= b) {
+      --p;
+      if (i < s.rank[p]) --r;
+    }
+    __syncwarp();
+    const int np = i + r;
+    if (live && np < L) {
+      s.keys[np] = key;
+      s.flags[np] = flag;
+    }
+    __syncwarp();
   }
   for (int j = lane; j < c; j += 32) {
-    const unsigned long long b = cand[j];
-    const int p = j + lower_bound_u64(s.cur_keys + pos0, s.len - pos0, b) + pos0;
-    if (p < L) {
-      s.nxt_keys[p] = b;
-      s.nxt_flags[p] = 0;
+    const int np = j + s.rank[j];
+    if (np < L) {
+      s.keys[np] = cand[j];
+      s.flags[np] = 0;
     }
   }
   __syncwarp();
-  unsigned long long* tk = s.cur_keys;
-  s.cur_keys = s.nxt_keys;
-  s.nxt_keys = tk;
-  unsigned char* tf = s.cur_flags;
-  s.cur_flags = s.nxt_flags;
-  s.nxt_flags = tf;
   s.len = (s.len + c < L) ? s.len + c : L;
   return pos0;
 }
@@ -251,7 +263,7 @@ __device__ __forceinline__ unsigned exact_dist_warp(const SearchArgs& a, const u
 
 template <int MODE, int NB>
 __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem& lay,
-                          uint32_t* vis, int qi, int lane) {
+                          uint32_t* vis, uint32_t* vlog, int qi, int lane) {
   const long long t0 = global_timer_ns();
   const int d = a.d, L = a.L, k = a.k, D = a.depth, n = a.n;
   const int log2cap = a.vis_log2;
@@ -267,10 +279,9 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
   const int slot_bytes = (MODE == kModePqU8) ? a.block_bytes : a.adj_stride * 4;
 
   QueryState s;
-  s.cur_keys = reinterpret_cast<unsigned long long*>(ws + lay.keys_a);
-  s.nxt_keys = reinterpret_cast<unsigned long long*>(ws + lay.keys_b);
-  s.cur_flags = ws + lay.flags_a;
-  s.nxt_flags = ws + lay.flags_b;
+  s.keys = reinterpret_cast<unsigned long long*>(ws + lay.keys);
+  s.flags = ws + lay.flags;
+  s.rank = reinterpret_cast<int*>(ws + lay.rank);
 
   // ---- query vector into shared memory
   {
@@ -308,9 +319,11 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
     entry_dist = exact_dist_warp<MODE>(a, qs, a.entry, lane);
   }
   if (lane == 0) {
-    s.cur_keys[0] = make_key(entry_dist, a.entry);
-    s.cur_flags[0] = 0;
-    atomicCAS(vis + hash_slot(a.entry, log2cap), 0u, static_cast<unsigned>(a.entry) + 1u);
+    s.keys[0] = make_key(entry_dist, a.entry);
+    s.flags[0] = 0;
+    const unsigned slot0 = hash_slot(a.entry, log2cap);
+    atomicCAS(vis + slot0, 0u, static_cast<unsigned>(a.entry) + 1u);
+    vlog[0] = slot0;
   }
   for (int j = lane; j < k; j += 32) res[j] = kNoKey;
   __syncwarp();
@@ -325,7 +338,7 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
     int sel = -1;
     for (int b = first_open; b < s.len; b += 32) {
       const int i = b + lane;
-      const unsigned m = __ballot_sync(kFull, i < s.len && s.cur_flags[i] == 0);
+      const unsigned m = __ballot_sync(kFull, i < s.len && s.flags[i] == 0);
       if (m) {
         sel = b + __ffs(m) - 1;
         break;
@@ -334,13 +347,13 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
     first_open = sel >= 0 ? sel + 1 : s.len;
     if (sel >= 0) {
       // ---- a4: issue the fetch of its block into the next ring slot
-      const unsigned long long key = s.cur_keys[sel];
+      const unsigned long long key = s.keys[sel];
       const unsigned v = static_cast<unsigned>(key);
       int slot = head + inflight;
       if (slot > D) slot -= D + 1;
       __syncwarp();
       if (lane == 0) {
-        s.cur_flags[sel] = 1;
+        s.flags[sel] = 1;
         ring_key[slot] = key;
       }
       const uint8_t* src = (MODE == kModePqU8)
@@ -435,9 +448,15 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
         }
         if (!__any_sync(kFull, any)) break;
       }
+      // append the newly used slots to this warp's clear log
       int nfresh = 0;
+      const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
-      for (int t = 0; t < NB; ++t) nfresh += __popc(__ballot_sync(kFull, fresh[t]));
+      for (int t = 0; t < NB; ++t) {
+        const unsigned m = __ballot_sync(kFull, fresh[t]);
+        if (fresh[t]) vlog[visited + nfresh + __popc(m & lt_mask)] = pos[t];
+        nfresh += __popc(m);
+      }
       visited += nfresh;
 
       // ---- a8: navigation distances of the unseen neighbours
@@ -513,13 +532,10 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
         ok ? ((MODE == kModeExactF32) ? __uint_as_float(dbits) : static_cast<float>(dbits))
            : __int_as_float(0x7f800000);
   }
-  // Clear the visited table for the next query of this warp.
-  {
-    uint4* t4 = reinterpret_cast<uint4*>(vis);
-    const int n4 = (1 << log2cap) >> 2;
-    const uint4 z = make_uint4(0, 0, 0, 0);
-    for (int j = lane; j < n4; j += 32) t4[j] = z;
-  }
+  // Clear the slots this query used, so the table is all zero for the next
+  // query of this warp.
+  __syncwarp();
+  for (int j = lane; j < visited; j += 32) vis[vlog[j]] = 0u;
   if (lane == 0) {
     if (a.steps) a.steps[qi] = steps;
     if (a.status) a.status[qi] = status;
@@ -544,12 +560,13 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp, int slot_bytes) {
   const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, slot_bytes, a.depth, a.L, a.k, NB);
   const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
   uint32_t* vis = a.vis + (gw << a.vis_log2);
+  uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
   for (;;) {
     int qi = 0;
     if (lane == 0) qi = atomicAdd(&a.counters[0], 1);
     qi = __shfl_sync(kFull, qi, 0);
     if (qi >= a.nq) break;
-    run_query<MODE, NB>(a, ws, lay, vis, qi, lane);
+    run_query<MODE, NB>(a, ws, lay, vis, vlog, qi, lane);
   }
 }
 
@@ -611,6 +628,7 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   int lg = 12;
   while ((1ll << lg) < want && lg < 22) ++lg;
   p.vis_log2 = lg;
+  p.vis_log_cap = (3 << lg) / 4 + 32 * p.nb + 1;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -188,28 +188,31 @@ def test_degenerate_graphs():
 
 
 def test_visited_overflow_reports_enomem():
-    """Host-side check of the device's failure path: a random graph of degree
-    128 and a list of 32 visits far more nodes than the visited table holds
-    (capacity 2*L*R slots, overflow above 3/4); the query must report
-    ANN_ENOMEM rather than diverge."""
-    rng = np.random.default_rng(5)
+    """The device's failure path, checked from the host: on a ring lattice
+    (node i -> i+1..i+R, positions on a line) a query at the far end makes the
+    search march through every node, so it visits all 60,000 while the
+    visited table holds next_pow2(2*R*(L+64)) = 32,768 slots (overflow above
+    3/4).  The query must report ANN_ENOMEM rather than diverge, and the index
+    must stay usable (its tables are cleared after the failed queries)."""
     n, R = 60_000, 128
-    base = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
-    # random out-neighbours, never the node itself (a repeated id in a row is
-    # simply seen as visited the second time)
-    adj = ((np.arange(n)[:, None] + 1 + rng.integers(0, n - 1, size=(n, R))) % n).astype(np.int32)
+    base = np.zeros((n, 4), np.float32)
+    base[:, 0] = np.arange(n, dtype=np.float32)
+    adj = ((np.arange(n)[:, None] + 1 + np.arange(R)[None, :]) % n).astype(np.int32)
     ix = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
     try:
-        q = rng.integers(0, 256, size=(3, 16)).astype(np.uint8)
+        q = np.zeros((3, 4), np.float32)
+        q[:, 0] = n - 1
         ids, dists, stats, tr = ix.search(q, 10, 32, 1, trace=True)
         assert np.all(tr["status"] == ann._abi.ANN_ENOMEM)
         assert stats.n_failed == 3 and stats.first_failed == 0
         with pytest.raises(ann.AnnError) as e:
             ix.search(q, 10, 32, 1)
         assert e.value.status == ann._abi.ANN_ENOMEM
-        # the tables were cleared after the failed queries: a repeat behaves the same
         ids2, dists2, stats2, tr2 = ix.search(q, 10, 32, 1, trace=True)
         assert np.array_equal(ids2, ids) and np.array_equal(tr2["steps"], tr["steps"])
+        # a query next to the entry node finishes normally on the same index
+        ok, okd, _ = ix.search(np.zeros((1, 4), np.float32), 3, 32, 1)
+        assert ok.tolist() == [[0, 1, 2]]
     finally:
         ix.close()
 
