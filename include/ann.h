@@ -164,6 +164,34 @@ int ann_search_dev(ann_index* index, const void* queries, int64_t nq, int32_t k,
 int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
 
 /*
+ * ann_search_dev without any allocation at call time.  The paper has no
+ * counterpart: this exists for callers that must not call cudaMalloc while
+ * they search -- a serving thread with a latency budget (cudaMalloc may
+ * synchronise the device), a process whose device memory is reserved up
+ * front by its own pool, or code that must not grow its footprint after
+ * start-up.  The search is the same kernel and gives the same results; its
+ * scratch (visited tables, their clear logs, counters) lives in one 32 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits.  The caller still passes queries and outputs
+ * (device memory, as for ann_search_dev) and loads the index beforehand.
+ *  - Limit: a call must fit the scratch of at least 16 warps; an (L, R) pair
+ *    needing more than 32 MiB / 16 per warp (e.g. L >= 2048 at R = 64) is
+ *    rejected with ANN_EINVAL.  Fewer resident warps than ann_search_dev may
+ *    use, so throughput is lower.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and zeroes what must start at zero, so
+ *    calls that overlap on the GPU race: serialise them (one stream, or
+ *    events).
+ *  - Enqueued on `stream`; returns once launched.  Per-query failures are
+ *    reported only through trace->status (device memory, may be NULL).
+ */
+int ann_search_dev_noalloc(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
+                           int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
+                           void* stream);
+
+/*
  * Train a product quantiser and encode the base (index-construction tooling;
  * runs on host threads).  The training sample is the first min(n, n_train)
  * rows.  Per subspace: k-means++ seeding (kpp_uniforms[m*256 + c] is the

@@ -150,6 +150,20 @@ class Index:
                                      ctypes.c_void_p(dists.data_ptr()),
                                      ctypes.byref(tr) if tr else None, st))
 
+    def search_dev_noalloc(self, queries, k: int, L: int, depth: int, ids, dists, stream=None,
+                           trace: dict | None = None):
+        """search_dev with its scratch in the library's fixed static device
+        array: no allocation at call time (see ann_search_dev_noalloc)."""
+        tr = None
+        if trace:
+            tr = Trace(**{key: ctypes.c_void_p(t.data_ptr()) for key, t in trace.items()})
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(_lib().ann_search_dev_noalloc(self._h, ctypes.c_void_p(queries.data_ptr()),
+                                             queries.shape[0], k, L, depth,
+                                             ctypes.c_void_p(ids.data_ptr()),
+                                             ctypes.c_void_p(dists.data_ptr()),
+                                             ctypes.byref(tr) if tr else None, st))
+
     def sync(self, stream=None) -> SearchStats:
         stats = SearchStats()
         st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)

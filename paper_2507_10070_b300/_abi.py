@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA"
 # Every symbol include/ann.h declares.
 EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_file",
            "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
-           "ann_search", "ann_search_dev", "ann_sync", "ann_build_pq", "ann_build_graph",
+           "ann_search", "ann_search_dev", "ann_sync", "ann_search_dev_noalloc",
+           "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_probe_read_bandwidth"]
 
 
@@ -78,6 +79,9 @@ def lib():
                                  ctypes.POINTER(SearchStats)]
         L.ann_search_dev.restype = ctypes.c_int
         L.ann_search_dev.argtypes = [P, P, I64, I32, I32, I32, P, P, ctypes.POINTER(Trace), P]
+        L.ann_search_dev_noalloc.restype = ctypes.c_int
+        L.ann_search_dev_noalloc.argtypes = [P, P, I64, I32, I32, I32, P, P,
+                                             ctypes.POINTER(Trace), P]
         L.ann_sync.restype = ctypes.c_int
         L.ann_sync.argtypes = [P, P, ctypes.POINTER(SearchStats)]
         L.ann_build_pq.restype = ctypes.c_int

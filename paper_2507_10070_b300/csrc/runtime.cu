@@ -619,3 +619,34 @@ int ann_load_graph_file(ann_index** out, const char* path, int32_t tier) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Read-only view of an index for other translation units of the library:
+// fills the index part of SearchArgs and the plan inputs.
+// ---------------------------------------------------------------------------
+namespace ann {
+
+int index_search_view(const ann_index* ix, SearchArgs* a, int* mode, int* slot_bytes) {
+  if (!ix) return set_error(ANN_EINVAL, "index is NULL");
+  *a = SearchArgs{};
+  a->n = (int32_t)ix->n;
+  a->d = ix->d;
+  a->R = ix->R;
+  a->entry = ix->entry;
+  a->M = ix->M;
+  a->dsub = ix->dsub;
+  a->blocks = ix->blocks_dev;
+  a->block_bytes = ix->block_bytes;
+  a->ids_off = ix->ids_off;
+  a->deg_off = ix->deg_off;
+  a->codes = ix->codes;
+  a->cb_words = ix->cb_words;
+  a->vectors = ix->vectors;
+  a->adj = ix->adj;
+  a->adj_stride = ix->adj_stride;
+  *mode = ix->mode;
+  *slot_bytes = ix->block_bytes;
+  return ANN_OK;
+}
+
+}  // namespace ann
