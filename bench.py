@@ -209,7 +209,8 @@ def run_ours(args, rank: int, world: int):
         per_depth[depth] = {"qps": nq / (np.median(ms) * 1e-3), "recall": round(r, 4),
                             "mean_steps": st.expansions / max(st.queries, 1)}
     best_depth = max((d for d in args.depths if d > 0), key=lambda d: per_depth[d]["qps"])
-    probe_gbps = ann.probe_read_bandwidth(1 << 30, ix.block_bytes, ann.ANN_TIER_HOST_PINNED, 64)
+    fetch_bytes = int(st.bytes_per_expansion)
+    probe_gbps = ann.probe_read_bandwidth(1 << 30, fetch_bytes, ann.ANN_TIER_HOST_PINNED, 64)
     setup_s = time.time() - t_setup
 
     # ---- timed region: K relaxed steps (the metric), then K synchronous steps
@@ -250,7 +251,7 @@ def run_ours(args, rank: int, world: int):
             e2e_ms.append((t1 - t0) * 1e3)
 
     # ---- roofline of the search kernel (storage-tier bound)
-    bytes_per_launch = st.expansions / args.steps * ix.block_bytes
+    bytes_per_launch = st.expansions / args.steps * st.bytes_per_expansion
     achieved = bytes_per_launch / (total_ms / args.steps * 1e-3) / 1e9
     qps = world * nq * args.steps / (total_ms * 1e-3)
     qps_sync = nq * args.steps / (float(np.sum(ms_sync)) * 1e-3)
@@ -261,6 +262,7 @@ def run_ours(args, rank: int, world: int):
         "data": "synthetic (seeded Gaussian mixture shaped like SIFT; index built in-run by the library's tooling)",
         "config": {"workload": WORKLOAD, "n": args.n, "nq": nq, "k": k, "L": chosen_L,
                    "depth": best_depth, "R": 64, "M": 32, "block_bytes": ix.block_bytes,
+                   "fetch_bytes_per_expansion": int(st.bytes_per_expansion),
                    "tier": "host_pinned", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world} (queries independent, no collective)"},
         "recall_at_10": round(recall, 4), "recall_at_10_sync": round(recall_sync, 4),
@@ -279,7 +281,7 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "pcie", "achieved": round(achieved, 2), "peak": round(probe_gbps, 2),
                      "unit": "GB/s", "frac": round(achieved / probe_gbps, 4), "traffic": None,
-                     "peak_source": "measured in-run: random 512 B node-block reads of host pinned memory by a full-occupancy probe kernel (ann_probe_read_bandwidth)",
+                     "peak_source": f"measured in-run: random {fetch_bytes} B reads of host pinned memory (the search's per-expansion fetch) by a full-occupancy probe kernel (ann_probe_read_bandwidth)",
                      "algorithmic_bytes_per_launch": int(bytes_per_launch),
                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs")},
         "setup_s": round(setup_s, 1),
@@ -362,9 +364,19 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--ref-L", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe-sweep", action="store_true",
+                    help="only print the storage-tier probe's GB/s for several read sizes")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.probe_sweep:
+        import paper_2507_10070_b300 as ann
+        out = {"probe": "random reads of a 1 GiB region, full-occupancy grid, 4 reads in flight per warp"}
+        for tier, name in ((ann.ANN_TIER_HOST_PINNED, "host_pinned_GBps"), (ann.ANN_TIER_HBM, "hbm_GBps")):
+            out[name] = {str(b): round(ann.probe_read_bandwidth(1 << 30, b, tier, 64), 2)
+                         for b in (128, 256, 384, 512, 1024, 2048, 4096)}
+        print(json.dumps(out), flush=True)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

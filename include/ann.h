@@ -95,7 +95,9 @@ typedef struct {
 typedef struct {
   int64_t queries;       /* queries searched */
   int64_t expansions;    /* node blocks fetched and expanded */
-  int64_t block_bytes;   /* bytes of one node block (PQ mode) or adjacency row */
+  int64_t bytes_per_expansion; /* bytes read from the node-block tier per expansion:
+                                  the vector and the neighbour ids (PQ mode), or
+                                  one adjacency row (exact navigation) */
   int32_t n_failed;      /* queries whose status is not ANN_OK */
   int32_t first_failed;  /* index of the first failed query, or -1 */
   float kernel_ms;       /* device time of the last search kernel (ann_search only) */
@@ -113,6 +115,8 @@ const char* ann_version(void);
  * (cudaHostAlloc, mapped) or HBM copies (ANN_ENOMEM / ANN_ECUDA on failure)
  * and uploads.  Node block layout: [vector: d*elt bytes][R int32 neighbour
  * ids, -1 padded][uint32 degree][zero pad to a multiple of 128 bytes].
+ * A search step fetches only the vector and the ids (the first d*elt + 4R
+ * bytes, rounded up to 16): the ids are -1 padded, so the degree is implied.
  * On success *out owns all of it until ann_free.  Uses the current device.
  */
 int ann_load_graph(ann_index** out, const ann_graph_desc* desc);

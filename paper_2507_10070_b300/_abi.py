@@ -42,7 +42,7 @@ class Trace(ctypes.Structure):
 
 class SearchStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("expansions", ctypes.c_int64),
-                ("block_bytes", ctypes.c_int64), ("n_failed", ctypes.c_int32),
+                ("bytes_per_expansion", ctypes.c_int64), ("n_failed", ctypes.c_int32),
                 ("first_failed", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
 
 

@@ -31,7 +31,8 @@ struct SearchArgs {
   const uint8_t* blocks;    // PQ mode: n node blocks (host-mapped or HBM)
   int32_t block_bytes;      // bytes per node block (multiple of 16)
   int32_t ids_off;          // byte offset of the neighbour ids in a block
-  int32_t deg_off;          // byte offset of the degree in a block
+  int32_t deg_off;          // byte offset of the degree in a block (not fetched)
+  int32_t slot_bytes;       // bytes fetched per expansion into a ring slot (multiple of 16)
   const uint8_t* codes;     // PQ mode: n*M codes (HBM)
   const uint32_t* cb_words; // PQ mode: M*256*(dsub/4) words, 4 uint8 coordinates each
   const void* vectors;      // exact modes: n*d elements (HBM)

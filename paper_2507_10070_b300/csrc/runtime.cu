@@ -66,6 +66,7 @@ struct ann_index {
   int64_t n = 0;
   int d = 0, dtype = 0, R = 0, entry = 0, M = 0, dsub = 0, tier = 0, mode = 0;
   int block_bytes = 0, ids_off = 0, deg_off = 0, adj_stride = 0;
+  int slot_bytes = 0;  // bytes fetched per expansion (vector + ids, or an adjacency row)
   uint8_t* blocks_host = nullptr;  // pinned host tier
   uint8_t* blocks_dev = nullptr;   // device-visible address of the blocks
   bool blocks_in_hbm = false;
@@ -196,6 +197,7 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
     ix->ids_off = d;
     ix->deg_off = d + 4 * R;
     ix->block_bytes = align_up(d + 4 * R + 4, 128);
+    ix->slot_bytes = align_up(d + 4 * R, 16);
     const size_t total = (size_t)n * ix->block_bytes;
     std::vector<uint8_t> tmp;
     uint8_t* dst;
@@ -252,6 +254,7 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
     ANN_TRY(cudaMemcpy(ix->vectors, g->vectors, vbytes, cudaMemcpyHostToDevice), "upload vectors");
     ix->adj_stride = align_up(R, 4);
     ix->block_bytes = ix->adj_stride * 4;
+    ix->slot_bytes = ix->block_bytes;
     std::vector<int32_t> rows((size_t)n * ix->adj_stride, -1);
     for (int64_t i = 0; i < n; ++i)
       for (int j = 0; j < R; ++j) {
@@ -286,7 +289,7 @@ int validate_search(const ann_index* ix, const void* q, int64_t nq, int k, int L
 int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int depth, int32_t* ids,
                    float* dists, const ann_trace* tr, cudaStream_t st, bool timed) {
   if (nq == 0) return ANN_OK;
-  const int slot_bytes = ix->block_bytes;
+  const int slot_bytes = ix->slot_bytes;
   SearchPlan plan;
   cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
@@ -322,6 +325,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   a.block_bytes = ix->block_bytes;
   a.ids_off = ix->ids_off;
   a.deg_off = ix->deg_off;
+  a.slot_bytes = ix->slot_bytes;
   a.codes = ix->codes;
   a.cb_words = ix->cb_words;
   a.vectors = ix->vectors;
@@ -371,7 +375,7 @@ int collect(ann_index* ix, cudaStream_t st, int64_t queries, ann_search_stats* s
   if (stats) {
     stats->queries = queries;
     stats->expansions = (int64_t)ex;
-    stats->block_bytes = ix->block_bytes;
+    stats->bytes_per_expansion = ix->slot_bytes;
     stats->n_failed = c[1];
     stats->first_failed = c[1] > 0 ? c[2] : -1;
     stats->kernel_ms = ms;
@@ -639,13 +643,14 @@ int index_search_view(const ann_index* ix, SearchArgs* a, int* mode, int* slot_b
   a->block_bytes = ix->block_bytes;
   a->ids_off = ix->ids_off;
   a->deg_off = ix->deg_off;
+  a->slot_bytes = ix->slot_bytes;
   a->codes = ix->codes;
   a->cb_words = ix->cb_words;
   a->vectors = ix->vectors;
   a->adj = ix->adj;
   a->adj_stride = ix->adj_stride;
   *mode = ix->mode;
-  *slot_bytes = ix->block_bytes;
+  *slot_bytes = ix->slot_bytes;
   return ANN_OK;
 }
 

@@ -276,7 +276,7 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
   unsigned long long* res = reinterpret_cast<unsigned long long*>(ws + lay.res);
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(ws + lay.cand);
   unsigned long long* ring_key = reinterpret_cast<unsigned long long*>(ws + lay.ring_key);
-  const int slot_bytes = (MODE == kModePqU8) ? a.block_bytes : a.adj_stride * 4;
+  const int slot_bytes = a.slot_bytes;
 
   QueryState s;
   s.keys = reinterpret_cast<unsigned long long*>(ws + lay.keys);
@@ -391,16 +391,9 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
       result_insert(res, s.nres, k, rkey, lane);
 
       // ---- a7: neighbour ids and the visited set
-      int deg;
-      const int32_t* nbr;
-      if (MODE == kModePqU8) {
-        deg = static_cast<int>(*reinterpret_cast<const unsigned*>(blk + a.deg_off));
-        deg = deg < a.R ? deg : a.R;
-        nbr = reinterpret_cast<const int32_t*>(blk + a.ids_off);
-      } else {
-        deg = a.R;
-        nbr = reinterpret_cast<const int32_t*>(blk);
-      }
+      // Neighbour ids are -1 padded, so the degree word need not be fetched.
+      const int deg = a.R;
+      const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + (MODE == kModePqU8 ? a.ids_off : 0));
       int w[NB];
       unsigned pos[NB];
       bool pending[NB], fresh[NB];
@@ -551,13 +544,13 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
 }
 
 template <int MODE, int NB>
-__global__ void search_kernel(SearchArgs a, int smem_per_warp, int slot_bytes) {
+__global__ void search_kernel(SearchArgs a, int smem_per_warp) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
   unsigned char* ws = smem + wib * smem_per_warp;
-  const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, slot_bytes, a.depth, a.L, a.k, NB);
+  const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
   const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
   uint32_t* vis = a.vis + (gw << a.vis_log2);
   uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
@@ -573,12 +566,10 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp, int slot_bytes) {
 template <int MODE, int NB>
 cudaError_t launch_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) {
   const int smem = p.smem_per_warp * p.warps_per_block;
-  const int slot_bytes = (MODE == kModePqU8) ? a.block_bytes : a.adj_stride * 4;
   cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  search_kernel<MODE, NB><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, p.smem_per_warp,
-                                                                          slot_bytes);
+  search_kernel<MODE, NB><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, p.smem_per_warp);
   return cudaGetLastError();
 }
 
