@@ -43,16 +43,18 @@ WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Va
 
 
 def prepare_sift_like(n: int = 1_000_000, nq: int = 10_000, R: int = 64, M: int = 32,
-                      L_build: int = 128, verbose: bool = True):
+                      L_build: int = 128, verbose: bool = True, builder: str = "cpu"):
     """Generate (or load from _data/) the SIFT-like workload and its index,
     built with the library's tooling: ann_build_pq (100k-vector training
-    sample, 25 Lloyd iterations) and ann_build_graph (Vamana, alpha 1.2)."""
+    sample, 25 Lloyd iterations) and Vamana (alpha 1.2) on host threads
+    (builder="cpu", ann_build_graph) or on the GPU (builder="gpu",
+    ann_build_graph_gpu)."""
     import paper_2507_10070_b300 as ann
     mx = datagen.sift_like()
     base = mx.base(n)
     q = mx.queries(nq)
     os.makedirs(DATA, exist_ok=True)
-    path = os.path.join(DATA, f"sift_like_n{n}_R{R}_M{M}_Lb{L_build}.npz")
+    path = os.path.join(DATA, f"sift_like_n{n}_R{R}_M{M}_Lb{L_build}_{builder}.npz")
     if os.path.exists(path):
         z = np.load(path)
         return dict(base=base, q=q, cb=z["cb"], codes=z["codes"], adj=z["adj"],
@@ -61,9 +63,10 @@ def prepare_sift_like(n: int = 1_000_000, nq: int = 10_000, R: int = 64, M: int 
     cb, codes = ann.build_pq(base, M, n_train=100_000, iters=25,
                              kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, M))
     t1 = time.time()
-    adj, entry = ann.build_graph(base, R, 1.2, L_build, seed=mx.seed)
+    adj, entry = ann.build_graph(base, R, 1.2, L_build, seed=mx.seed, device=builder)
     if verbose:
-        print(f"# index built: pq {t1 - t:.1f}s, graph {time.time() - t1:.1f}s", file=sys.stderr)
+        print(f"# index built: pq {t1 - t:.1f}s, graph ({builder}) {time.time() - t1:.1f}s",
+              file=sys.stderr)
     tmp = path + f".{os.getpid()}.tmp.npz"
     np.savez(tmp, cb=cb, codes=codes, adj=adj, entry=entry)
     os.replace(tmp, path)
@@ -150,7 +153,9 @@ def run_ours(args, rank: int, world: int):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     t_setup = time.time()
-    w = prepare_sift_like(args.n, args.nq)
+    t_idx = time.time()
+    w = prepare_sift_like(args.n, args.nq, builder=args.builder)
+    index_build_s = time.time() - t_idx
     gt_ids, gt_d = ground_truth(w)
     ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],
                    tier=ann.ANN_TIER_HOST_PINNED)
@@ -285,13 +290,108 @@ def run_ours(args, rank: int, world: int):
                      "algorithmic_bytes_per_launch": int(bytes_per_launch),
                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs")},
         "setup_s": round(setup_s, 1),
+        "index": {"builder": args.builder, "seconds_incl_pq_and_data": round(index_build_s, 1)},
     }
+    if args.serve_seconds > 0:
+        out["serving"] = run_serving(ix, w, gt_ids, gt_d, chosen_L, best_depth, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, chosen_L, args.cpu_sample)
     if rank == 0:
         out["clocks"] = clk.summary()
     ix.close()
     return out
+
+
+def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
+                load: float = 0.7, seed: int = 7):
+    """Continuous-batching request loop.  Requests are batches of queries with
+    size log-uniform in [1, 512], k in {10, 100} and L in {L*, 1.25 L*, 1.5 L*}
+    (L* = the batch operating point).  Phase 1 keeps the server saturated to
+    measure its capacity; phase 2 offers a seeded Poisson stream of requests at
+    `load` x that capacity and measures each request's latency from its
+    arrival (admission waits included) to its results in host memory."""
+    import paper_2507_10070_b300 as ann
+    rng = np.random.default_rng(seed)
+    Ls = [L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32]
+    nq_all = w["q"].shape[0]
+
+    def draw(n):
+        sizes = np.minimum(512, np.exp(rng.uniform(0, np.log(512), n)).astype(int))
+        return sizes, rng.choice([10, 100], n), rng.choice(Ls, n), rng.integers(0, nq_all - 512, n)
+
+    srv = ann.Server(ix, max_L=max(Ls), max_k=100, depth=depth, slots=16384, idle_exit_us=100_000)
+    hits = [0.0, 0]
+
+    def collect(meta, on_done):
+        for rid in srv.ready(0):
+            ids, d, info = srv.poll(rid, 0)
+            j = meta.pop(rid)
+            on_done(j)
+            s0, n = starts[j], sizes[j]
+            hits[0] += ann.recall_at_k(ids[:, :10], gt_ids[s0:s0 + n], gt_d[s0:s0 + n], d[:, :10]) * n
+            hits[1] += n
+
+    try:
+        # phase 1: saturation (closed loop, ring kept full)
+        n_req = 4000
+        sizes, ks, Lq, starts = draw(n_req)
+        meta, i, done_q = {}, 0, [0]
+        t0 = time.perf_counter()
+        while (i < n_req or meta) and time.perf_counter() - t0 < seconds:
+            while i < n_req:
+                try:
+                    rid = srv.submit(w["q"][starts[i]:starts[i] + sizes[i]], int(ks[i]), int(Lq[i]))
+                except ann.AnnError as e:
+                    if e.status != ann._abi.ANN_EBUSY:
+                        raise
+                    break
+                meta[rid] = i
+                i += 1
+            collect(meta, lambda j: done_q.__setitem__(0, done_q[0] + sizes[j]))
+            time.sleep(2e-4)
+        t_sat = time.perf_counter() - t0
+        while meta:
+            collect(meta, lambda j: None)
+            time.sleep(2e-4)
+        capacity = done_q[0] / t_sat
+        # phase 2: Poisson arrivals at `load` x capacity
+        mean_batch = 511.0 / np.log(512.0)
+        rate = load * capacity / mean_batch
+        n_req = max(1, int(rate * seconds))
+        sizes, ks, Lq, starts = draw(n_req)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        lat = []
+        meta, i = {}, 0
+        hits[0], hits[1] = 0.0, 0
+        t0 = time.perf_counter()
+        while i < n_req or meta:
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                try:
+                    rid = srv.submit(w["q"][starts[i]:starts[i] + sizes[i]], int(ks[i]), int(Lq[i]))
+                except ann.AnnError as e:
+                    if e.status != ann._abi.ANN_EBUSY:
+                        raise
+                    break
+                meta[rid] = i
+                i += 1
+            collect(meta, lambda j: lat.append(time.perf_counter() - t0 - arrivals[j]))
+            time.sleep(5e-5)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"what": "continuous-batching request loop (ann_serve_*): saturation capacity, then Poisson arrivals of request batches",
+            "capacity_qps": round(capacity, 1), "offered_qps": round(load * capacity, 1),
+            "value": round(int(sizes.sum()) / wall, 1), "unit": "queries/s", "requests": n_req,
+            "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 2),
+                           "p99": round(float(np.percentile(lat_ms, 99)), 2),
+                           "what": "per request, arrival to results in host memory"},
+            "recall_at_10": round(hits[0] / max(hits[1], 1), 4), "L_choices": Ls,
+            "k_choices": [10, 100], "batch_size": "log-uniform [1, 512]",
+            "kernel_launches": int(st.launches), "resident_warps": int(st.resident_warps),
+            "seconds": round(wall, 2)}
 
 
 def cpu_baseline(w, L: int, sample: int):
@@ -316,7 +416,7 @@ def run_reference(args):
     the GPU arm's rule (smallest L with recall@10 >= 0.95), judged on the first
     200 queries against the oracle's own brute-force ground truth."""
     import oracle
-    w = prepare_sift_like(args.n, args.nq)
+    w = prepare_sift_like(args.n, args.nq, builder=args.builder)
     threads = oracle.default_threads()
     qs = w["q"][:200]
     gi, gd = oracle.knn(w["base"], qs, 10, threads)
@@ -364,6 +464,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--ref-L", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of the serving (request loop) measurement; 0 skips it")
+    ap.add_argument("--builder", choices=["cpu", "gpu"], default="gpu",
+                    help="Vamana construction for the index (off the clock)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only print the storage-tier probe's GB/s for several read sizes")
     args = ap.parse_args()

@@ -174,14 +174,15 @@ int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
  * synchronise the device), a process whose device memory is reserved up
  * front by its own pool, or code that must not grow its footprint after
  * start-up.  The search is the same kernel and gives the same results; its
- * scratch (visited tables, their clear logs, counters) lives in one 32 MiB
+ * scratch (visited tables, their clear logs, counters) lives in one 16 MiB
  * device array inside the library, which every GPU that loads the library
  * holds until the process exits.  The caller still passes queries and outputs
  * (device memory, as for ann_search_dev) and loads the index beforehand.
- *  - Limit: a call must fit the scratch of at least 16 warps; an (L, R) pair
- *    needing more than 32 MiB / 16 per warp (e.g. L >= 2048 at R = 64) is
- *    rejected with ANN_EINVAL.  Fewer resident warps than ann_search_dev may
- *    use, so throughput is lower.
+ *  - Limit: a call must fit the scratch of at least 32 warps; an (L, R) pair
+ *    needing more than 16 MiB / 32 = 512 KiB per warp (R > 64 with
+ *    L > 2048) is rejected with ANN_EINVAL.  At most 16 MiB / (per-warp
+ *    scratch) warps run, fewer than ann_search_dev may use, so throughput
+ *    is lower.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress with that device current); make that first call
  *    before any stream capture.
@@ -194,6 +195,77 @@ int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
 int ann_search_dev_noalloc(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
                            int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
                            void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over one index.
+ *
+ * The paper evaluates batched search; its I/O stack lets every query proceed
+ * independently of the others (Section "Resource-Efficient Query-Grained
+ * Concurrent I/O Stack": no synchronisation across queries).  This loop puts
+ * that property to work for requests that arrive over time: each request is
+ * a batch of queries with its own k and L; its queries become work items in
+ * a ring of `slots` staging entries (mapped pinned host memory), admitted
+ * while slots are free.  A persistent kernel keeps one query per resident
+ * warp and a warp that finishes takes the next item of any request, so new
+ * requests start as warps free up and overlap with running ones on the
+ * device.  Results are written to host memory by the kernel.  A query's
+ * results do not depend on what else is in flight.
+ * ------------------------------------------------------------------------ */
+typedef struct ann_server ann_server; /* opaque */
+
+typedef struct {
+  int32_t max_L;        /* largest L a request may use (sets the shared-memory layout), <= 4096 */
+  int32_t max_k;        /* largest k, <= min(max_L, 256) */
+  int32_t depth;        /* relaxed-pipeline depth 0..4 used for every query */
+  int32_t slots;        /* staging ring size: queries queued or in flight at once */
+  int32_t idle_exit_us; /* the kernel returns after this long without work (bounded polling);
+                           it is relaunched when new work arrives */
+} ann_serve_cfg;
+
+typedef struct {
+  int64_t queries;     /* queries of the request */
+  int64_t expansions;  /* node blocks fetched for them */
+  int32_t n_failed;    /* queries that overflowed their visited set */
+  int64_t device_ns;   /* device time from the first query's start to the last one's end */
+} ann_serve_result;
+
+typedef struct {
+  int64_t launches;       /* serving-kernel launches so far */
+  int64_t published;      /* queries admitted so far */
+  int64_t retired;        /* queries whose results were collected */
+  int64_t resident_warps; /* queries the kernel works on at once */
+  int32_t running;        /* 1 if the kernel is running now */
+} ann_serve_counters;
+
+/* Create a server (allocates the staging ring, scratch and a host launcher
+ * thread; uses the current device).  The index must outlive the server. */
+int ann_serve_create(ann_index* index, const ann_serve_cfg* cfg, ann_server** out);
+
+/* Admit a request of nq queries (host memory, the index's dtype), 1 <= k <=
+ * max_k, k <= L <= max_L.  Copies the queries; returns ANN_EBUSY if fewer
+ * than nq staging slots are free (nothing is admitted then).  Thread-safe. */
+int ann_serve_submit(ann_server* server, const void* queries, int64_t nq, int32_t k, int32_t L,
+                     uint64_t* req_id);
+
+/* Wait up to timeout_us (0: just check) for a request.  On completion copies
+ * its nq*k ids and dists to host memory (same layout as ann_search), fills
+ * `info` (may be NULL), frees its slots and forgets the request; returns
+ * ANN_ETIMEOUT if it is not done yet (call again), ANN_ENOMEM if a query
+ * overflowed its visited set (results copied all the same). */
+int ann_serve_poll(ann_server* server, uint64_t req_id, int32_t* ids, float* dists,
+                   int64_t timeout_us, ann_serve_result* info);
+
+/* Wait up to timeout_us (0: just check) until at least one admitted request
+ * is complete; writes up to `max` ids of complete, not yet collected requests
+ * to req_ids and their number to *n_ready (0 on timeout).  Collect each with
+ * ann_serve_poll (it returns at once). */
+int ann_serve_poll_any(ann_server* server, uint64_t* req_ids, int32_t max, int64_t timeout_us,
+                       int32_t* n_ready);
+
+int ann_serve_stats(ann_server* server, ann_serve_counters* out);
+
+/* Stop the kernel (after the queries in progress) and free everything. */
+void ann_serve_destroy(ann_server* server);
 
 /*
  * Train a product quantiser and encode the base (index-construction tooling;
@@ -220,6 +292,56 @@ int ann_build_pq(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t 
 int ann_build_graph(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
                     float alpha, int32_t L_build, uint64_t seed, int32_t nthreads,
                     int32_t* adj_out, int32_t* entry_out);
+
+/*
+ * Computation / I/O balanced degree selector (Section "Sampling-Based Graph
+ * Degree Selector": the workflow and its Eq. d = argmin_d |T_c(d) - T_f(d)|).
+ * For each candidate degree a sample index of n_sample random uint8 vectors
+ * with random links, random PQ codes (M subspaces) and an integer codebook is
+ * built and a batch of nq random queries is searched at list size L (depth
+ * 0), once with the node blocks in HBM and once in host pinned memory.
+ * t_compute_us is the mean search time per step with the blocks in HBM (a
+ * step is then its computation plus a short HBM fetch); t_fetch_us is the
+ * extra time per step with the blocks in host memory.  *best_degree is the
+ * degree with the smallest |t_compute - t_fetch|; at that degree the pipeline
+ * depth 0..4 with the highest measured queries/s is *best_depth, and the
+ * five measured rates go to depth_qps (may be NULL).  Warps per query are
+ * one in this kernel.  Uses the current device; takes seconds.
+ */
+typedef struct {
+  int32_t n_sample;        /* sample size (the paper suggests ~100k) */
+  int32_t d;               /* dimension of the workload (multiple of 16) */
+  int32_t M;               /* PQ subspaces of the workload (multiple of 16) */
+  const int32_t* degrees;  /* candidate degrees, each 1..128 */
+  int32_t n_degrees;
+  int32_t L;               /* list size used for the measurement */
+  int32_t nq;              /* sample queries per measurement (>= 32) */
+  uint64_t seed;
+} ann_autotune_cfg;
+
+typedef struct {
+  int32_t degree;
+  float t_compute_us;  /* per-step time, node blocks in HBM */
+  float t_fetch_us;    /* extra per-step time, node blocks in host memory */
+  float step_us_sync;  /* per-step time, node blocks in host memory, depth 0 */
+  float qps_sync;      /* queries per second of that run */
+} ann_autotune_point;
+
+int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
+                        int32_t* best_degree, int32_t* best_depth, float* depth_qps);
+
+/*
+ * The same Vamana construction on the GPU (index-build tooling): the batch
+ * searches run on the library's search kernel (exact navigation on the
+ * vectors in HBM), RobustPrune runs one warp per node, and back edges are
+ * grouped by a device sort.  The candidate pool of a node is the L_build
+ * expanded nodes nearest to it.  Deterministic.  Needs d % 16 == 0,
+ * 1 <= R <= 64, R <= L_build <= 256 - R.  Uses the current device; host
+ * buffers in and out, as ann_build_graph.
+ */
+int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                        float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
+                        int32_t* entry_out);
 
 /*
  * Exact k nearest neighbours by brute force on the GPU (ground truth).

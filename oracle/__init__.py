@@ -61,7 +61,7 @@ def _load():
         lib.orc_pq_encode.argtypes = [I, P, I64, I, I, I, P, P]
         lib.orc_search.restype = I
         lib.orc_search.argtypes = [I, P, I64, I, I, P, I, P, P, ctypes.c_int32, P, I64,
-                                   I, I, I, P, P, P, P, I, I]
+                                   I, I, I, P, P, P, P, I, P, I]
         lib.orc_vamana.restype = I
         lib.orc_vamana.argtypes = [I, P, I64, I, I, D, I, ctypes.c_int32, P, P, I, P]
         _lib = lib
@@ -140,13 +140,14 @@ def pq_encode(base: np.ndarray, codebook: np.ndarray) -> np.ndarray:
 def search(base: np.ndarray, adj: np.ndarray, entry: int, queries: np.ndarray, k: int,
            L: int, depth: int, codebook: np.ndarray | None = None,
            codes: np.ndarray | None = None, threads: int | None = None,
-           trace_cap: int = 0):
+           trace_cap: int = 0, return_visited: bool = False):
     """Best-first search with relaxed fetch depth `depth` (0 = synchronous).
 
     Navigation uses PQ codes when `codebook`/`codes` are given, exact
     distances otherwise.  Returns (ids int32 (nq,k), dists float64 (nq,k),
     steps int32 (nq,)) and, with trace_cap > 0, the expansion sequences
-    (nq, trace_cap) padded with -1.
+    (nq, trace_cap) padded with -1; with return_visited, also the number of
+    distinct nodes each query inserted into its visited set (last element).
     """
     base = _c(base)
     adj = _c(adj, np.int32)
@@ -163,15 +164,15 @@ def search(base: np.ndarray, adj: np.ndarray, entry: int, queries: np.ndarray, k
     dists = np.empty((nq, k), np.float64)
     steps = np.empty(nq, np.int32)
     trace = np.full((nq, trace_cap), -1, np.int32) if trace_cap else None
+    nvis = np.empty(nq, np.int32) if return_visited else None
     rc = _load().orc_search(_dtype_code(base), _ptr(base), n, d, adj.shape[1], _ptr(adj), M,
                             _ptr(codebook), _ptr(codes), entry, _ptr(queries), nq, k, L, depth,
                             _ptr(ids), _ptr(dists), _ptr(steps), _ptr(trace), trace_cap,
-                            threads or default_threads())
+                            _ptr(nvis), threads or default_threads())
     if rc != 0:
         raise ValueError("oracle search: invalid arguments")
-    if trace_cap:
-        return ids, dists, steps, trace
-    return ids, dists, steps
+    out = (ids, dists, steps) + ((trace,) if trace_cap else ())
+    return out + (nvis,) if return_visited else out
 
 
 def vamana(base: np.ndarray, R: int, alpha: float, L_build: int, entry: int,

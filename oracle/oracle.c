@@ -416,8 +416,9 @@ typedef struct {
 static int search_one(const index_t* ix, const void* q, int k, int L, int D,
                       unsigned char* visited, cand_t* list, int32_t* fifo,
                       pair_t** results, int64_t* results_cap, int32_t* ids_out,
-                      double* dists_out, int32_t* expanded_out, int expanded_cap) {
-  int len = 0, fhead = 0, fcount = 0, steps = 0;
+                      double* dists_out, int32_t* expanded_out, int expanded_cap,
+                      int32_t* nvisited_out) {
+  int len = 0, fhead = 0, fcount = 0, steps = 0, nvisited = 1;
   int64_t nres = 0;
   memset(visited, 0, (size_t)ix->n);
   list[0].key.dist = nav_dist(ix, q, ix->entry);
@@ -456,6 +457,7 @@ static int search_one(const index_t* ix, const void* q, int k, int L, int D,
         if (w < 0) break;
         if (visited[w]) continue;
         visited[w] = 1;
+        ++nvisited;
         cand_t e;
         e.key.dist = nav_dist(ix, q, w);
         e.key.id = w;
@@ -474,6 +476,7 @@ static int search_one(const index_t* ix, const void* q, int k, int L, int D,
     }
   }
   qsort(*results, (size_t)nres, sizeof(pair_t), pair_cmp);
+  if (nvisited_out) *nvisited_out = nvisited;
   for (int j = 0; j < k; ++j) {
     ids_out[j] = j < nres ? (*results)[j].id : -1;
     dists_out[j] = j < nres ? (*results)[j].dist : INFINITY;
@@ -490,6 +493,7 @@ typedef struct {
   int32_t* steps;
   int32_t* expanded;
   int expanded_cap;
+  int32_t* nvisited;
 } search_ctx;
 
 static void search_range(void* p, int64_t lo, int64_t hi) {
@@ -505,7 +509,7 @@ static void search_range(void* p, int64_t lo, int64_t hi) {
     int s = search_one(ix, q, c->k, c->L, c->D, visited, list, fifo, &res, &cap,
                        c->ids + qi * c->k, c->dists + qi * c->k,
                        c->expanded ? c->expanded + qi * c->expanded_cap : NULL,
-                       c->expanded_cap);
+                       c->expanded_cap, c->nvisited ? c->nvisited + qi : NULL);
     if (c->steps) c->steps[qi] = s;
   }
   free(visited);
@@ -518,11 +522,11 @@ int orc_search(int dtype, const void* base, int64_t n, int d, int R, const int32
                int M, const float* codebook, const uint8_t* codes, int32_t entry,
                const void* queries, int64_t nq, int k, int L, int D, int32_t* ids,
                double* dists, int32_t* steps, int32_t* expanded, int expanded_cap,
-               int nthreads) {
+               int32_t* nvisited, int nthreads) {
   if (k < 1 || L < k || D < 0 || n < 1 || entry < 0 || entry >= n) return -1;
   if (M > 0 && d % M != 0) return -1;
   index_t ix = {dtype, base, n, d, R, adj, M, codebook, codes, entry};
-  search_ctx c = {&ix, queries, k, L, D, ids, dists, steps, expanded, expanded_cap};
+  search_ctx c = {&ix, queries, k, L, D, ids, dists, steps, expanded, expanded_cap, nvisited};
   parallel_for(nq, nthreads, search_range, &c);
   return 0;
 }

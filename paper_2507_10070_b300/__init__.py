@@ -19,7 +19,8 @@ from . import _abi
 from ._abi import (ANN_F32, ANN_TIER_HBM, ANN_TIER_HOST_PINNED, ANN_U8, AnnError,
                    GraphDesc, SearchStats, Trace)
 
-__all__ = ["Index", "AnnError", "build_pq", "build_graph", "knn_exact", "probe_read_bandwidth",
+__all__ = ["Index", "Server", "AnnError", "build_pq", "build_graph", "knn_exact", "probe_read_bandwidth",
+           "autotune_degree",
            "recall_at_k", "library_path", "ANN_U8", "ANN_F32", "ANN_TIER_HOST_PINNED",
            "ANN_TIER_HBM", "save_index"]
 
@@ -171,6 +172,65 @@ class Index:
         return stats
 
 
+class Server:
+    """Continuous-batching request loop over an Index (see ann_serve_*)."""
+
+    def __init__(self, index: Index, max_L: int = 256, max_k: int = 100, depth: int = 1,
+                 slots: int = 16384, idle_exit_us: int = 2000):
+        self.index = index
+        self.max_k = max_k
+        self._h = ctypes.c_void_p()
+        cfg = _abi.ServeCfg(max_L=max_L, max_k=max_k, depth=depth, slots=slots,
+                            idle_exit_us=idle_exit_us)
+        _check(_lib().ann_serve_create(index._h, ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._k = {}
+
+    def submit(self, queries, k: int, L: int) -> int:
+        """Admit a request; returns its id (raises AnnError ANN_EBUSY when full)."""
+        q = _c(queries, self.index._np_dtype())
+        rid = ctypes.c_uint64(0)
+        _check(_lib().ann_serve_submit(self._h, _p(q), q.shape[0], k, L, ctypes.byref(rid)))
+        self._k[rid.value] = (q.shape[0], k)
+        return rid.value
+
+    def poll(self, req_id: int, timeout_us: int = 0):
+        """(ids, dists, info) once the request is done, or None if not yet."""
+        nq, k = self._k[req_id]
+        ids = np.empty((nq, k), np.int32)
+        dists = np.empty((nq, k), np.float32)
+        info = _abi.ServeResult()
+        rc = _lib().ann_serve_poll(self._h, req_id, _p(ids), _p(dists), timeout_us,
+                                   ctypes.byref(info))
+        if rc == _abi.ANN_ETIMEOUT:
+            return None
+        del self._k[req_id]
+        _check(rc)
+        return ids, dists, info
+
+    def ready(self, timeout_us: int = 0, max_n: int = 4096):
+        """Ids of admitted requests that are complete (not yet collected)."""
+        buf = (ctypes.c_uint64 * max_n)()
+        n = ctypes.c_int32(0)
+        _check(_lib().ann_serve_poll_any(self._h, buf, max_n, timeout_us, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    def stats(self):
+        st = _abi.ServeStats()
+        _check(_lib().ann_serve_stats(self._h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self._h:
+            _lib().ann_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def build_pq(base, M: int, n_train: int = 100_000, iters: int = 25, kpp_uniforms=None,
              seed: int = 0, threads: int = 0):
     """Train a PQ codebook on the first n_train rows and encode every row.
@@ -186,16 +246,42 @@ def build_pq(base, M: int, n_train: int = 100_000, iters: int = 25, kpp_uniforms
 
 
 def build_graph(base, R: int, alpha: float = 1.2, L_build: int = 128, seed: int = 0,
-                threads: int = 0):
-    """Vamana graph on host threads.  Returns (adj int32 (n,R), entry)."""
+                threads: int = 0, device: str = "cpu"):
+    """Vamana graph on host threads (device="cpu") or on the GPU
+    (device="gpu").  Returns (adj int32 (n,R), entry)."""
     base = _c(base)
     n, d = base.shape
     adj = np.empty((n, R), np.int32)
     entry = ctypes.c_int32(0)
-    _check(_lib().ann_build_graph(_p(base), _dtype_code(base), n, d, R, ctypes.c_float(alpha),
-                                  L_build, ctypes.c_uint64(seed), threads, _p(adj),
-                                  ctypes.byref(entry)))
+    if device == "gpu":
+        _check(_lib().ann_build_graph_gpu(_p(base), _dtype_code(base), n, d, R,
+                                          ctypes.c_float(alpha), L_build, ctypes.c_uint64(seed),
+                                          _p(adj), ctypes.byref(entry)))
+    else:
+        _check(_lib().ann_build_graph(_p(base), _dtype_code(base), n, d, R, ctypes.c_float(alpha),
+                                      L_build, ctypes.c_uint64(seed), threads, _p(adj),
+                                      ctypes.byref(entry)))
     return adj, int(entry.value)
+
+
+def autotune_degree(degrees=(32, 48, 64, 96), n_sample: int = 100_000, d: int = 128,
+                    M: int = 32, L: int = 32, nq: int = 4096, seed: int = 1):
+    """The paper's computation / I/O balanced degree selector on random-link
+    sample indices.  Returns a dict with the per-degree table, the chosen
+    degree (argmin |T_c - T_f|) and the fastest depth at that degree."""
+    deg = np.ascontiguousarray(np.asarray(degrees, np.int32))
+    cfg = _abi.AutotuneCfg(n_sample=n_sample, d=d, M=M, degrees=deg.ctypes.data,
+                           n_degrees=len(deg), L=L, nq=nq, seed=seed)
+    pts = (_abi.AutotunePoint * len(deg))()
+    best_d, best_depth = ctypes.c_int32(0), ctypes.c_int32(0)
+    qps = np.zeros(5, np.float32)
+    _check(_lib().ann_autotune_degree(ctypes.byref(cfg), pts, ctypes.byref(best_d),
+                                      ctypes.byref(best_depth), _p(qps)))
+    table = [{"degree": p.degree, "t_compute_us": round(p.t_compute_us, 3),
+              "t_fetch_us": round(p.t_fetch_us, 3), "step_us_sync": round(p.step_us_sync, 3),
+              "qps_sync": round(p.qps_sync, 1)} for p in pts]
+    return {"table": table, "degree": best_d.value, "depth": best_depth.value,
+            "qps_by_depth": [round(float(x), 1) for x in qps], "warps_per_query": 1}
 
 
 def knn_exact(base, queries, k: int):

@@ -19,7 +19,9 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
            "ann_search", "ann_search_dev", "ann_sync", "ann_search_dev_noalloc",
            "ann_build_pq", "ann_build_graph",
-           "ann_knn_exact", "ann_probe_read_bandwidth"]
+           "ann_knn_exact", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
+           "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
+           "ann_autotune_degree", "ann_build_graph_gpu"]
 
 
 class AnnError(RuntimeError):
@@ -44,6 +46,34 @@ class SearchStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("expansions", ctypes.c_int64),
                 ("bytes_per_expansion", ctypes.c_int64), ("n_failed", ctypes.c_int32),
                 ("first_failed", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("max_L", ctypes.c_int32), ("max_k", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("idle_exit_us", ctypes.c_int32)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("expansions", ctypes.c_int64),
+                ("n_failed", ctypes.c_int32), ("device_ns", ctypes.c_int64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("published", ctypes.c_int64),
+                ("retired", ctypes.c_int64), ("resident_warps", ctypes.c_int64),
+                ("running", ctypes.c_int32)]
+
+
+class AutotuneCfg(ctypes.Structure):
+    _fields_ = [("n_sample", ctypes.c_int32), ("d", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("degrees", ctypes.c_void_p), ("n_degrees", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("nq", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class AutotunePoint(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("t_compute_us", ctypes.c_float),
+                ("t_fetch_us", ctypes.c_float), ("step_us_sync", ctypes.c_float),
+                ("qps_sync", ctypes.c_float)]
 
 
 _lib = None
@@ -89,9 +119,29 @@ def lib():
         L.ann_build_graph.restype = ctypes.c_int
         L.ann_build_graph.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, I32, P,
                                       ctypes.POINTER(ctypes.c_int32)]
+        L.ann_build_graph_gpu.restype = ctypes.c_int
+        L.ann_build_graph_gpu.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, P,
+                                          ctypes.POINTER(ctypes.c_int32)]
         L.ann_knn_exact.restype = ctypes.c_int
         L.ann_knn_exact.argtypes = [P, I32, I64, I32, P, I64, I32, P, P]
         L.ann_probe_read_bandwidth.restype = ctypes.c_int
         L.ann_probe_read_bandwidth.argtypes = [I64, I32, I32, I32, ctypes.POINTER(ctypes.c_double)]
+        L.ann_serve_create.restype = ctypes.c_int
+        L.ann_serve_create.argtypes = [P, ctypes.POINTER(ServeCfg), ctypes.POINTER(ctypes.c_void_p)]
+        L.ann_serve_submit.restype = ctypes.c_int
+        L.ann_serve_submit.argtypes = [P, P, I64, I32, I32, ctypes.POINTER(ctypes.c_uint64)]
+        L.ann_serve_poll.restype = ctypes.c_int
+        L.ann_serve_poll.argtypes = [P, U64, P, P, I64, ctypes.POINTER(ServeResult)]
+        L.ann_serve_poll_any.restype = ctypes.c_int
+        L.ann_serve_poll_any.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), I32, I64,
+                                         ctypes.POINTER(ctypes.c_int32)]
+        L.ann_autotune_degree.restype = ctypes.c_int
+        L.ann_autotune_degree.argtypes = [ctypes.POINTER(AutotuneCfg), ctypes.POINTER(AutotunePoint),
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32), P]
+        L.ann_serve_stats.restype = ctypes.c_int
+        L.ann_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+        L.ann_serve_destroy.restype = None
+        L.ann_serve_destroy.argtypes = [P]
         _lib = L
     return _lib

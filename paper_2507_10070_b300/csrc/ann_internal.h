@@ -56,6 +56,27 @@ struct SearchArgs {
   unsigned long long* expansions;  // running total of expansions
 };
 
+// The serving kernel's view of a server's shared state.  Fields marked
+// "host" are mapped pinned host memory written or read by the host while the
+// kernel runs; the rest is device memory.
+struct ServeArgs {
+  const unsigned long long* tail;  // host: number of work items published
+  const int* stop;                 // host: nonzero asks the kernel to return
+  unsigned long long* head;        // device: number of work items claimed
+  unsigned long long* tail_mirror; // device: latest tail value seen by a polling warp
+  unsigned long long* last_claim;  // device: device timer at the latest claim by any warp
+  const int32_t* item_kL;          // host: [slots][2] k and L of each item
+  const uint8_t* qbuf;             // host: [slots][qbytes] query vectors
+  int32_t* rids;                   // host: [slots][max_k]
+  float* rdists;                   // host: [slots][max_k]
+  int32_t* rsteps;                 // host: [slots]
+  int32_t* rstatus;                // host: [slots]
+  int64_t* rtimes;                 // host: [slots][2] device timer at start and end
+  unsigned long long* done;        // host: [slots] item number + 1 once its results are written
+  int32_t slots, qbytes, max_k;
+  long long idle_ns;               // return after this long without work
+};
+
 // Launch geometry and shared-memory layout derived from the arguments.
 struct SearchPlan {
   int mode;
@@ -107,6 +128,9 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
 cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
                         int64_t nq, SearchPlan* plan);
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream);
+// Persistent serving kernel (a.L / a.k are the largest L / k it accepts).
+cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,
+                         cudaStream_t stream);
 
 // Storage-tier read probe kernel launcher.
 cudaError_t launch_read_probe(const uint8_t* region, int64_t nblocks, int block_bytes, int iters,

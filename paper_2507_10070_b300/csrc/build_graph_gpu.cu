@@ -1,0 +1,458 @@
+// ann_build_graph_gpu: Vamana graph construction on the GPU (index-build
+// tooling, off the search path).  Same algorithm and batch schedule as the
+// host builder (build_graph.cpp): random start graph, one pass with alpha = 1
+// and one with `alpha`, nodes inserted in batches that grow geometrically up
+// to 2% of n, every search of a batch reading the graph as it stood before
+// the batch.
+//
+// Per batch:
+//  1. gather the batch's vectors;
+//  2. GreedySearch(entry, x_p, L_build) for all of them at once with the
+//     library's search kernel (exact navigation on the vectors in HBM,
+//     depth 0); the L_build expanded nodes nearest to x_p form the candidate
+//     pool (DiskANN uses the whole expanded set, which is these plus the few
+//     expanded nodes that fell below them);
+//  3. RobustPrune(p, pool u N(p)) -- one warp per node (prune_kernel);
+//  4. back edges j <- p: the (j, p) pairs are sorted on the device (CUB
+//     radix sort), grouped by j, and each target appends its new sources or,
+//     if they do not fit in R, prunes N(j) u sources (prune_kernel again).
+// alpha is compared with squared distances (DiskANN's convention).  Every
+// step is deterministic, so the graph does not depend on timing.
+#include <cub/cub.cuh>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "ann_internal.h"
+
+namespace ann {
+namespace {
+
+constexpr int kCandMax = 256;  // candidates one prune task considers
+constexpr unsigned kFull = 0xffffffffu;
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gather_rows(const uint8_t* __restrict__ base, int row_bytes,
+                            const int32_t* __restrict__ ids, int n, uint8_t* __restrict__ out) {
+  const int r = blockIdx.x;
+  if (r >= n) return;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(base + (size_t)ids[r] * row_bytes);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(out + (size_t)r * row_bytes);
+  for (int j = threadIdx.x; j < row_bytes / 4; j += blockDim.x) dst[j] = src[j];
+}
+
+// Squared distance between rows a and b, computed by one thread.
+template <bool U8>
+__device__ __forceinline__ float row_dist(const void* base, int d, int a, int b) {
+  if (U8) {
+    const uint4* x = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(base) + (size_t)a * d);
+    const uint4* y = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(base) + (size_t)b * d);
+    unsigned acc = 0;
+    for (int j = 0; j < d / 16; ++j) {
+      const uint4 u = __ldg(x + j), v = __ldg(y + j);
+      unsigned t;
+      t = __vabsdiffu4(u.x, v.x); acc = __dp4a(t, t, acc);
+      t = __vabsdiffu4(u.y, v.y); acc = __dp4a(t, t, acc);
+      t = __vabsdiffu4(u.z, v.z); acc = __dp4a(t, t, acc);
+      t = __vabsdiffu4(u.w, v.w); acc = __dp4a(t, t, acc);
+    }
+    return static_cast<float>(acc);
+  } else {
+    const float4* x = reinterpret_cast<const float4*>(static_cast<const float*>(base) + (size_t)a * d);
+    const float4* y = reinterpret_cast<const float4*>(static_cast<const float*>(base) + (size_t)b * d);
+    float acc = 0.f;
+    for (int j = 0; j < d / 4; ++j) {
+      const float4 u = __ldg(x + j), v = __ldg(y + j);
+      float t;
+      t = u.x - v.x; acc = fmaf(t, t, acc);
+      t = u.y - v.y; acc = fmaf(t, t, acc);
+      t = u.z - v.z; acc = fmaf(t, t, acc);
+      t = u.w - v.w; acc = fmaf(t, t, acc);
+    }
+    return acc;
+  }
+}
+
+__device__ __forceinline__ unsigned long long pkey(float d, int id) {
+  return (static_cast<unsigned long long>(__float_as_uint(d)) << 32) | static_cast<unsigned>(id);
+}
+
+// One warp per task: candidates = the node's current row (if include_row)
+// plus extra ids; deduplicated, self removed, sorted by (distance, id).  If
+// `append_if_fits` and they fit in R they become the row; otherwise
+// RobustPrune keeps <= R of them.  Rows are adj_stride ids, -1 padded.
+template <bool U8>
+__global__ void prune_kernel(const void* __restrict__ base, int d, int R, float alpha,
+                             const int32_t* __restrict__ task_node,
+                             const int32_t* __restrict__ extra, const int64_t* __restrict__ extra_off,
+                             const int32_t* __restrict__ extra_cnt, int ntasks, int include_row,
+                             int append_if_fits, int32_t* __restrict__ adj, int adj_stride) {
+  __shared__ unsigned long long keys[4][kCandMax];
+  __shared__ unsigned char gone[4][kCandMax];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int task = blockIdx.x * 4 + wib;
+  if (task >= ntasks) return;  // warp-uniform
+  unsigned long long* K = keys[wib];
+  unsigned char* G = gone[wib];
+  const int p = task_node[task];
+  int32_t* row = adj + (size_t)p * adj_stride;
+  // collect candidate ids
+  int nrow = 0;
+  if (include_row)
+    for (int j = 0; j < R; ++j) {
+      if (row[j] < 0) break;
+      ++nrow;
+    }
+  const int ne = min(extra_cnt[task], kCandMax - nrow);
+  const int32_t* ex = extra + extra_off[task];
+  const int nc = nrow + ne;
+  for (int c = lane; c < kCandMax; c += 32) {
+    unsigned long long key = ~0ull;
+    if (c < nc) {
+      const int id = c < nrow ? row[c] : ex[c - nrow];
+      if (id >= 0 && id != p) key = pkey(row_dist<U8>(base, d, p, id), id);
+    }
+    K[c] = key;
+  }
+  __syncwarp();
+  // sort 256 keys (bitonic, shared memory, 8 compare-exchanges per lane per stage)
+  for (int size = 2; size <= kCandMax; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < kCandMax; i += 32) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool asc = (i & size) == 0;
+          const unsigned long long a = K[i], b = K[j];
+          if ((a > b) == asc) {
+            K[i] = b;
+            K[j] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // drop duplicates (equal keys are adjacent), count valid
+  for (int c = lane; c < kCandMax; c += 32) G[c] = (K[c] == ~0ull || (c > 0 && K[c] == K[c - 1])) ? 1 : 0;
+  __syncwarp();
+  int valid = 0;
+  for (int c = lane; c < kCandMax; c += 32) valid += G[c] ? 0 : 1;
+  for (int o = 16; o > 0; o >>= 1) valid += __shfl_xor_sync(kFull, valid, o);
+  int kept = 0;
+  if (append_if_fits && valid <= R) {
+    // every unique candidate fits: it becomes the row
+    for (int c = 0; c < kCandMax; ++c) {
+      if (G[c]) continue;
+      if (lane == 0) row[kept] = static_cast<int32_t>(K[c] & 0xffffffffu);
+      ++kept;
+    }
+  } else {
+    for (int i = 0; i < kCandMax && kept < R; ++i) {
+      if (G[i]) continue;  // warp-uniform (shared memory, synced)
+      const int ci = static_cast<int>(K[i] & 0xffffffffu);
+      if (lane == 0) row[kept] = ci;
+      ++kept;
+      for (int j = i + 1 + lane; j < kCandMax; j += 32) {
+        if (G[j]) continue;
+        const int cj = static_cast<int>(K[j] & 0xffffffffu);
+        const float dpj = __uint_as_float(static_cast<unsigned>(K[j] >> 32));
+        if (alpha * row_dist<U8>(base, d, ci, cj) <= dpj) G[j] = 1;
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  for (int j = kept + lane; j < adj_stride; j += 32) row[j] = -1;
+}
+
+// (j << 32 | p) for every new edge p -> j of the batch; ~0 for empty slots.
+__global__ void edge_pairs(const int32_t* __restrict__ nodes, int b, const int32_t* __restrict__ adj,
+                           int adj_stride, int R, unsigned long long* __restrict__ pairs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b * R) return;
+  const int i = t / R, j = t % R;
+  const int p = nodes[i];
+  const int q = adj[(size_t)p * adj_stride + j];
+  pairs[t] = q >= 0 ? ((static_cast<unsigned long long>(q) << 32) | static_cast<unsigned>(p)) : ~0ull;
+}
+
+// Group starts of the sorted pairs: flags and the source ids; the empty
+// (~0) keys sort last and the first of them marks the number of valid pairs
+// (meta[1], preset to m).
+__global__ void group_marks(const unsigned long long* __restrict__ sorted, int m,
+                            int32_t* __restrict__ src, int32_t* __restrict__ is_start,
+                            int32_t* __restrict__ target, int32_t* __restrict__ meta) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const unsigned long long k = sorted[t];
+  src[t] = static_cast<int32_t>(k & 0xffffffffu);
+  target[t] = static_cast<int32_t>(k >> 32);
+  is_start[t] = (k != ~0ull) && (t == 0 || (sorted[t - 1] >> 32) != (k >> 32));
+  if (k == ~0ull && (t == 0 || sorted[t - 1] != ~0ull)) meta[1] = t;
+}
+
+__global__ void group_tasks(const int32_t* __restrict__ starts, int g, int m_valid,
+                            const int32_t* __restrict__ target, int32_t* __restrict__ task_node,
+                            int64_t* __restrict__ off, int32_t* __restrict__ cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g) return;
+  const int s = starts[t];
+  const int e = t + 1 < g ? starts[t + 1] : m_valid;
+  task_node[t] = target[s];
+  off[t] = s;
+  cnt[t] = e - s;
+}
+
+__global__ void iota(int32_t* __restrict__ out, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = t;
+}
+
+__global__ void fill_pool_meta(int b, int Lb, int64_t* __restrict__ off, int32_t* __restrict__ cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b) return;
+  off[t] = (int64_t)t * Lb;
+  cnt[t] = Lb;
+}
+
+template <class T>
+cudaError_t dmalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+}  // namespace
+}  // namespace ann
+
+using namespace ann;
+
+extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                                   float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
+                                   int32_t* entry_out) {
+  if (!base || !adj_out) return set_error(ANN_EINVAL, "ann_build_graph_gpu: NULL buffer");
+  if (dtype != ANN_U8 && dtype != ANN_F32) return set_error(ANN_EINVAL, "ann_build_graph_gpu: unknown dtype");
+  if (n < 2 || n >= INT32_MAX || R < 1 || R > 64 || L_build < R || L_build > kCandMax - R ||
+      d < 16 || d % 16 || d > kMaxD || !(alpha >= 1.0f))
+    return set_error(ANN_EINVAL,
+                     "ann_build_graph_gpu: need 2 <= n, 1 <= R <= 64, R <= L_build <= %d - R, d %% 16 == 0 "
+                     "(n=%lld d=%d R=%d L=%d)", kCandMax, (long long)n, d, R, L_build);
+  const int elt = dtype == ANN_U8 ? 1 : 4;
+  const int row_bytes = d * elt;
+  const int stride = align_up(R, 4);
+  // medoid on the host (float64 mean, lowest id on ties), as the host builder
+  int64_t entry = 0;
+  {
+    const int th = std::max(1u, std::thread::hardware_concurrency());
+    std::vector<double> mean(d, 0.0);
+    std::vector<std::vector<double>> part(th, std::vector<double>(d, 0.0));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < th; ++t)
+      pool.emplace_back([&, t] {
+        for (int64_t i = t * n / th; i < (t + 1) * n / th; ++i)
+          for (int j = 0; j < d; ++j)
+            part[t][j] += dtype == ANN_U8 ? static_cast<const uint8_t*>(base)[i * d + j]
+                                          : static_cast<double>(static_cast<const float*>(base)[i * d + j]);
+      });
+    for (auto& x : pool) x.join();
+    pool.clear();
+    for (int t = 0; t < th; ++t)
+      for (int j = 0; j < d; ++j) mean[j] += part[t][j];
+    for (double& m : mean) m /= static_cast<double>(n);
+    std::vector<double> bd(th, INFINITY);
+    std::vector<int64_t> bi(th, -1);
+    for (int t = 0; t < th; ++t)
+      pool.emplace_back([&, t] {
+        for (int64_t i = t * n / th; i < (t + 1) * n / th; ++i) {
+          double s = 0.0;
+          for (int j = 0; j < d; ++j) {
+            const double v = (dtype == ANN_U8 ? static_cast<const uint8_t*>(base)[i * d + j]
+                                              : static_cast<double>(static_cast<const float*>(base)[i * d + j])) - mean[j];
+            s += v * v;
+          }
+          if (s < bd[t]) {
+            bd[t] = s;
+            bi[t] = i;
+          }
+        }
+      });
+    for (auto& x : pool) x.join();
+    double best = INFINITY;
+    for (int t = 0; t < th; ++t)
+      if (bi[t] >= 0 && bd[t] < best) {
+        best = bd[t];
+        entry = bi[t];
+      }
+  }
+  // random start graph and insertion order (host), as the host builder
+  std::vector<int32_t> adj((size_t)n * stride, -1);
+  uint64_t rs = seed;
+  const int init_deg = static_cast<int>(std::min<int64_t>(R, n - 1));
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t* row = &adj[(size_t)i * stride];
+    int c = 0;
+    while (c < init_deg) {
+      const int32_t v = static_cast<int32_t>(splitmix64(rs) % static_cast<uint64_t>(n));
+      if (v == i) continue;
+      bool dup = false;
+      for (int j = 0; j < c; ++j) dup |= row[j] == v;
+      if (!dup) row[c++] = v;
+    }
+  }
+  std::vector<int32_t> order(n);
+  for (int64_t i = 0; i < n; ++i) order[i] = static_cast<int32_t>(i);
+  for (int64_t i = n - 1; i > 0; --i) std::swap(order[i], order[splitmix64(rs) % static_cast<uint64_t>(i + 1)]);
+
+  const int64_t max_batch = std::max<int64_t>(1, n / 50);
+  const int mode = dtype == ANN_U8 ? kModeExactU8 : kModeExactF32;
+  SearchPlan plan;
+  cudaError_t e = plan_search(mode, R, 0, d, stride * 4, 0, L_build, L_build, max_batch, &plan);
+  if (e != cudaSuccess) return cuda_error(e, "plan build search");
+  const size_t nwarps = (size_t)plan.blocks * plan.warps_per_block;
+  uint8_t *base_d = nullptr, *qbuf = nullptr;
+  int32_t *adj_d = nullptr, *order_d = nullptr, *cand_ids = nullptr, *counters = nullptr;
+  float* cand_d = nullptr;
+  uint32_t *vis = nullptr, *vlog = nullptr;
+  unsigned long long *exp_d = nullptr, *pairs = nullptr, *sorted = nullptr;
+  int32_t *src = nullptr, *is_start = nullptr, *target = nullptr, *starts = nullptr, *nsel = nullptr;
+  int32_t *task_node = nullptr, *cnt = nullptr, *idx = nullptr;
+  int64_t* off = nullptr;
+  void* cub_tmp = nullptr;
+  size_t cub_bytes = 0, sel_bytes = 0;
+  const size_t pmax = (size_t)max_batch * R;
+  auto cleanup = [&]() {
+    cudaFree(base_d); cudaFree(qbuf); cudaFree(adj_d); cudaFree(order_d); cudaFree(cand_ids);
+    cudaFree(counters); cudaFree(cand_d); cudaFree(vis); cudaFree(vlog); cudaFree(exp_d);
+    cudaFree(pairs); cudaFree(sorted); cudaFree(src); cudaFree(is_start); cudaFree(target);
+    cudaFree(starts); cudaFree(nsel); cudaFree(task_node); cudaFree(cnt); cudaFree(off); cudaFree(cub_tmp);
+    cudaFree(idx);
+  };
+#define GB_TRY(call, what)          \
+  do {                              \
+    e = (call);                     \
+    if (e != cudaSuccess) {         \
+      cleanup();                    \
+      return cuda_error(e, what);   \
+    }                               \
+  } while (0)
+  GB_TRY(dmalloc(&base_d, (size_t)n * row_bytes), "cudaMalloc vectors");
+  GB_TRY(cudaMemcpy(base_d, base, (size_t)n * row_bytes, cudaMemcpyHostToDevice), "upload vectors");
+  GB_TRY(dmalloc(&adj_d, adj.size()), "cudaMalloc adjacency");
+  GB_TRY(cudaMemcpy(adj_d, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice), "upload adjacency");
+  GB_TRY(dmalloc(&order_d, (size_t)n), "cudaMalloc order");
+  GB_TRY(cudaMemcpy(order_d, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice), "upload order");
+  GB_TRY(dmalloc(&qbuf, (size_t)max_batch * row_bytes), "cudaMalloc batch");
+  GB_TRY(dmalloc(&cand_ids, (size_t)max_batch * L_build), "cudaMalloc candidates");
+  GB_TRY(dmalloc(&cand_d, (size_t)max_batch * L_build), "cudaMalloc candidates");
+  GB_TRY(dmalloc(&vis, nwarps << plan.vis_log2), "cudaMalloc visited");
+  GB_TRY(cudaMemset(vis, 0, (nwarps << plan.vis_log2) * 4), "cudaMemset");
+  GB_TRY(dmalloc(&vlog, nwarps * plan.vis_log_cap), "cudaMalloc visited log");
+  GB_TRY(dmalloc(&counters, 4), "cudaMalloc counters");
+  GB_TRY(dmalloc(&exp_d, 1), "cudaMalloc counters");
+  GB_TRY(dmalloc(&pairs, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&sorted, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&src, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&is_start, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&target, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&starts, pmax), "cudaMalloc pairs");
+  GB_TRY(dmalloc(&nsel, 2), "cudaMalloc pairs");  // [0] groups, [1] valid pairs
+  GB_TRY(dmalloc(&idx, pmax), "cudaMalloc pairs");
+  iota<<<(unsigned)((pmax + 255) / 256), 256>>>(idx, (int)pmax);
+  GB_TRY(dmalloc(&task_node, std::max<size_t>(pmax, (size_t)max_batch)), "cudaMalloc tasks");
+  GB_TRY(dmalloc(&cnt, std::max<size_t>(pmax, (size_t)max_batch)), "cudaMalloc tasks");
+  GB_TRY(dmalloc(&off, std::max<size_t>(pmax, (size_t)max_batch)), "cudaMalloc tasks");
+  GB_TRY(cub::DeviceRadixSort::SortKeys(nullptr, cub_bytes, pairs, sorted, (int)pmax), "cub sizing");
+  GB_TRY(cub::DeviceSelect::Flagged(nullptr, sel_bytes, idx, is_start,
+                                    starts, nsel, (int)pmax), "cub sizing");
+  GB_TRY(dmalloc(reinterpret_cast<uint8_t**>(&cub_tmp), std::max(cub_bytes, sel_bytes)), "cudaMalloc sort scratch");
+  cudaStream_t st = 0;
+
+  SearchArgs a{};
+  a.n = (int32_t)n;
+  a.d = d;
+  a.R = R;
+  a.entry = (int32_t)entry;
+  a.M = 0;
+  a.vectors = base_d;
+  a.adj = adj_d;
+  a.adj_stride = stride;
+  a.slot_bytes = stride * 4;
+  a.block_bytes = stride * 4;
+  a.queries = qbuf;
+  a.k = L_build;
+  a.L = L_build;
+  a.depth = 0;
+  a.ids = cand_ids;
+  a.dists = cand_d;
+  a.vis = vis;
+  a.vis_log2 = plan.vis_log2;
+  a.vis_log = vlog;
+  a.vis_log_cap = plan.vis_log_cap;
+  a.counters = counters;
+  a.expansions = exp_d;
+
+  const size_t max_cub = std::max(cub_bytes, sel_bytes);
+  for (int pass = 0; pass < 2; ++pass) {
+    const float al = pass == 0 ? 1.0f : alpha;
+    int64_t done = 0, batch = 1;
+    while (done < n) {
+      const int b = (int)std::min(batch, n - done);
+      const int32_t* nodes = order_d + done;
+      gather_rows<<<b, 128, 0, st>>>(base_d, row_bytes, nodes, b, qbuf);
+      GB_TRY(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), st), "reset counter");
+      SearchPlan pb = plan;
+      pb.blocks = (int)std::min<int64_t>(plan.blocks, b);
+      a.nq = b;
+      GB_TRY(launch_search(a, pb, st), "build search");
+      // forward prune: pool = the search results, plus the current row
+      fill_pool_meta<<<(b + 255) / 256, 256, 0, st>>>(b, L_build, off, cnt);
+      if (dtype == ANN_U8)
+        prune_kernel<true><<<(b + 3) / 4, 128, 0, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, b, 1, 0, adj_d, stride);
+      else
+        prune_kernel<false><<<(b + 3) / 4, 128, 0, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, b, 1, 0, adj_d, stride);
+      // back edges
+      const int m = b * R;
+      edge_pairs<<<(m + 255) / 256, 256, 0, st>>>(nodes, b, adj_d, stride, R, pairs);
+      size_t tb = max_cub;
+      GB_TRY(cub::DeviceRadixSort::SortKeys(cub_tmp, tb, pairs, sorted, m, 0, 64, st), "sort edges");
+      const int32_t preset[2] = {0, m};
+      GB_TRY(cudaMemcpyAsync(nsel, preset, sizeof(preset), cudaMemcpyHostToDevice, st), "group meta");
+      group_marks<<<(m + 255) / 256, 256, 0, st>>>(sorted, m, src, is_start, target, nsel);
+      tb = max_cub;
+      GB_TRY(cub::DeviceSelect::Flagged(cub_tmp, tb, idx, is_start, starts,
+                                        nsel, m, st), "group edges");
+      int32_t meta[2] = {0, 0};
+      GB_TRY(cudaMemcpyAsync(meta, nsel, sizeof(meta), cudaMemcpyDeviceToHost, st), "group count");
+      GB_TRY(cudaStreamSynchronize(st), "build batch");
+      const int32_t g = meta[0], m_valid = meta[1];
+      if (g > 0) {
+        group_tasks<<<(g + 255) / 256, 256, 0, st>>>(starts, g, m_valid, target, task_node, off, cnt);
+        if (dtype == ANN_U8)
+          prune_kernel<true><<<(g + 3) / 4, 128, 0, st>>>(base_d, d, R, al, task_node, src, off, cnt, g, 1, 1, adj_d, stride);
+        else
+          prune_kernel<false><<<(g + 3) / 4, 128, 0, st>>>(base_d, d, R, al, task_node, src, off, cnt, g, 1, 1, adj_d, stride);
+      }
+      GB_TRY(cudaGetLastError(), "build kernels");
+      done += b;
+      batch = std::min<int64_t>(batch * 2, max_batch);
+    }
+  }
+  GB_TRY(cudaStreamSynchronize(st), "build");
+  std::vector<int32_t> rows((size_t)n * stride);
+  GB_TRY(cudaMemcpy(rows.data(), adj_d, rows.size() * 4, cudaMemcpyDeviceToHost), "download adjacency");
+  for (int64_t i = 0; i < n; ++i)
+    std::memcpy(adj_out + (size_t)i * R, rows.data() + (size_t)i * stride, (size_t)R * 4);
+  if (entry_out) *entry_out = (int32_t)entry;
+  cleanup();
+#undef GB_TRY
+  return ANN_OK;
+}

@@ -261,11 +261,24 @@ __device__ __forceinline__ unsigned exact_dist_warp(const SearchArgs& a, const u
   }
 }
 
+// One query's parameters and output locations.
+struct QueryJob {
+  const void* query;   // query vector; NULL if the caller already put it in shared memory
+  int k, L;
+  int qi;              // query number, for failure reporting
+  int32_t* ids;        // [k]
+  float* dists;        // [k]
+  int32_t* steps;      // single values, each may be NULL
+  int32_t* status;
+  int64_t* t_begin;
+  int64_t* t_end;
+};
+
 template <int MODE, int NB>
-__device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem& lay,
-                          uint32_t* vis, uint32_t* vlog, int qi, int lane) {
+__device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned char* ws,
+                          const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int lane) {
   const long long t0 = global_timer_ns();
-  const int d = a.d, L = a.L, k = a.k, D = a.depth, n = a.n;
+  const int d = a.d, L = job.L, k = job.k, D = a.depth, n = a.n;
   const int log2cap = a.vis_log2;
   const unsigned cap_mask = (1u << log2cap) - 1u;
   const int vis_limit = (3 << log2cap) >> 2;  // overflow above 3/4 load
@@ -284,10 +297,9 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
   s.rank = reinterpret_cast<int*>(ws + lay.rank);
 
   // ---- query vector into shared memory
-  {
+  if (job.query) {
     const int qbytes = (MODE == kModeExactF32) ? d * 4 : d;
-    const unsigned* src = reinterpret_cast<const unsigned*>(
-        static_cast<const uint8_t*>(a.queries) + static_cast<size_t>(qi) * qbytes);
+    const unsigned* src = static_cast<const unsigned*>(job.query);
     unsigned* dst = reinterpret_cast<unsigned*>(qs);
     for (int j = lane; j < (qbytes >> 2); j += 32) dst[j] = __ldg(src + j);
   }
@@ -421,44 +433,33 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
           }
         }
       }
-      for (int probe = 0; probe <= static_cast<int>(cap_mask); ++probe) {
-        bool any = false;
+      // Visited set, first round: one CAS on every neighbour's home slot, in
+      // flight together with the code loads above.
+      unsigned old[NB];
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          if (pending[t]) {
-            const unsigned want = static_cast<unsigned>(w[t]) + 1u;
-            const unsigned old = atomicCAS(vis + pos[t], 0u, want);
-            if (old == 0u) {
-              fresh[t] = true;
-              pending[t] = false;
-            } else if (old == want) {
-              pending[t] = false;
-            } else {
-              pos[t] = (pos[t] + 1u) & cap_mask;
-              any = true;
-            }
-          }
-        }
-        if (!__any_sync(kFull, any)) break;
-      }
-      // append the newly used slots to this warp's clear log
-      int nfresh = 0;
-      const unsigned lt_mask = (1u << lane) - 1u;
+      for (int t = 0; t < NB; ++t)
+        old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
-        const unsigned m = __ballot_sync(kFull, fresh[t]);
-        if (fresh[t]) vlog[visited + nfresh + __popc(m & lt_mask)] = pos[t];
-        nfresh += __popc(m);
+        if (pending[t]) {
+          if (old[t] == 0u) {
+            fresh[t] = true;
+            pending[t] = false;
+          } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
+            pending[t] = false;  // seen before
+          } else {
+            pos[t] = (pos[t] + 1u) & cap_mask;  // collided: decided below
+          }
+        }
       }
-      visited += nfresh;
 
-      // ---- a8: navigation distances of the unseen neighbours
+      // ---- a8: navigation distances of the neighbours not known to be seen
       unsigned long long key[NB];
       if (MODE == kModePqU8) {
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
-          if (fresh[t]) {
+          if (fresh[t] || pending[t]) {
             unsigned dist = 0;
 #pragma unroll
             for (int c = 0; c < kMaxM / 16; ++c) {
@@ -481,7 +482,7 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
-          unsigned m = __ballot_sync(kFull, fresh[t]);
+          unsigned m = __ballot_sync(kFull, fresh[t] || pending[t]);
           while (m) {
             const int src_lane = __ffs(m) - 1;
             m &= m - 1;
@@ -492,14 +493,87 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
         }
       }
 
-      // ---- a9: sort the new keys, merge into the list, truncate to L
-      if (nfresh > 0) {
-        warp_bitonic_sort<NB>(key, lane);
+      // A key at or above the L-th entry of a full list can never enter: the
+      // L-th key only decreases while the list stays full, and navigation
+      // distances are fixed per query.  Such a node's visited status cannot
+      // change any later step, so a collided one is not probed further.
+      const unsigned long long thr = (s.len == L) ? s.keys[L - 1] : kNoKey;
 #pragma unroll
-        for (int t = 0; t < NB; ++t) cand[t * 32 + lane] = key[t];
-        __syncwarp();
-        const int changed = merge_candidates(s, cand, nfresh, L, lane);
-        if (changed < first_open) first_open = changed;
+      for (int t = 0; t < NB; ++t)
+        if (pending[t] && key[t] >= thr) pending[t] = false;
+      for (int probe = 0; probe < static_cast<int>(cap_mask); ++probe) {
+        bool any = false;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) any |= pending[t];
+        if (!__any_sync(kFull, any)) break;
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+          old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if (pending[t]) {
+            if (old[t] == 0u) {
+              fresh[t] = true;
+              pending[t] = false;
+            } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
+              pending[t] = false;
+            } else {
+              pos[t] = (pos[t] + 1u) & cap_mask;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        if (!fresh[t]) key[t] = kNoKey;
+
+      // append the newly used slots to this warp's clear log
+      int nfresh = 0;
+      const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const unsigned m = __ballot_sync(kFull, fresh[t]);
+        if (fresh[t]) vlog[visited + nfresh + __popc(m & lt_mask)] = pos[t];
+        nfresh += __popc(m);
+      }
+      visited += nfresh;
+
+      // ---- a9: sort the new keys that can enter (below the L-th entry of a
+      // full list), merge them into the list, truncate to L
+      if (nfresh > 0) {
+        int c = 0;
+        unsigned keep_mask[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          keep_mask[t] = __ballot_sync(kFull, key[t] < thr);
+          c += __popc(keep_mask[t]);
+        }
+        if (c > 0 && c <= 32) {
+          // compact the entering keys into one register per lane, sort 32
+          int base = 0;
+#pragma unroll
+          for (int t = 0; t < NB; ++t) {
+            if ((keep_mask[t] >> lane) & 1u) cand[base + __popc(keep_mask[t] & lt_mask)] = key[t];
+            base += __popc(keep_mask[t]);
+          }
+          __syncwarp();
+          unsigned long long one[1] = {lane < c ? cand[lane] : kNoKey};
+          __syncwarp();
+          warp_bitonic_sort<1>(one, lane);
+          cand[lane] = one[0];
+          __syncwarp();
+        } else if (c > 32) {
+#pragma unroll
+          for (int t = 0; t < NB; ++t) key[t] = key[t] < thr ? key[t] : kNoKey;
+          warp_bitonic_sort<NB>(key, lane);
+#pragma unroll
+          for (int t = 0; t < NB; ++t) cand[t * 32 + lane] = key[t];
+          __syncwarp();
+        }
+        if (c > 0) {
+          const int changed = merge_candidates(s, cand, c, L, lane);
+          if (changed < first_open) first_open = changed;
+        }
       }
       __syncwarp();
 
@@ -519,25 +593,24 @@ __device__ void run_query(const SearchArgs& a, unsigned char* ws, const WarpSmem
   for (int j = lane; j < k; j += 32) {
     const unsigned long long r = j < s.nres ? res[j] : kNoKey;
     const bool ok = r != kNoKey;
-    a.ids[static_cast<size_t>(qi) * k + j] = ok ? static_cast<int32_t>(r & 0xffffffffu) : -1;
+    job.ids[j] = ok ? static_cast<int32_t>(r & 0xffffffffu) : -1;
     const unsigned dbits = static_cast<unsigned>(r >> 32);
-    a.dists[static_cast<size_t>(qi) * k + j] =
-        ok ? ((MODE == kModeExactF32) ? __uint_as_float(dbits) : static_cast<float>(dbits))
-           : __int_as_float(0x7f800000);
+    job.dists[j] = ok ? ((MODE == kModeExactF32) ? __uint_as_float(dbits) : static_cast<float>(dbits))
+                      : __int_as_float(0x7f800000);
   }
   // Clear the slots this query used, so the table is all zero for the next
   // query of this warp.
   __syncwarp();
   for (int j = lane; j < visited; j += 32) vis[vlog[j]] = 0u;
   if (lane == 0) {
-    if (a.steps) a.steps[qi] = steps;
-    if (a.status) a.status[qi] = status;
-    if (a.t_begin) a.t_begin[qi] = t0;
-    if (a.t_end) a.t_end[qi] = global_timer_ns();
+    if (job.steps) *job.steps = steps;
+    if (job.status) *job.status = status;
+    if (job.t_begin) *job.t_begin = t0;
+    if (job.t_end) *job.t_end = global_timer_ns();
     atomicAdd(a.expansions, static_cast<unsigned long long>(steps));
     if (status != ANN_OK) {
       atomicAdd(&a.counters[1], 1);
-      atomicMin(&a.counters[2], qi);
+      atomicMin(&a.counters[2], job.qi);
     }
   }
   __syncwarp();
@@ -559,8 +632,144 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
     if (lane == 0) qi = atomicAdd(&a.counters[0], 1);
     qi = __shfl_sync(kFull, qi, 0);
     if (qi >= a.nq) break;
-    run_query<MODE, NB>(a, ws, lay, vis, vlog, qi, lane);
+    QueryJob job;
+    const int qbytes = (MODE == kModeExactF32) ? a.d * 4 : a.d;
+    job.query = static_cast<const uint8_t*>(a.queries) + static_cast<size_t>(qi) * qbytes;
+    job.k = a.k;
+    job.L = a.L;
+    job.qi = qi;
+    job.ids = a.ids + static_cast<size_t>(qi) * a.k;
+    job.dists = a.dists + static_cast<size_t>(qi) * a.k;
+    job.steps = a.steps ? a.steps + qi : nullptr;
+    job.status = a.status ? a.status + qi : nullptr;
+    job.t_begin = a.t_begin ? a.t_begin + qi : nullptr;
+    job.t_end = a.t_end ? a.t_end + qi : nullptr;
+    run_query<MODE, NB>(a, job, ws, lay, vis, vlog, lane);
   }
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_sys_u32(const void* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Persistent serving kernel: every warp claims published work items one at a
+// time (atomicCAS on the device head, against the published tail), runs the
+// search for it and writes the results straight into mapped host memory,
+// then the item's done word.  Work items of different requests and of
+// different k and L share the warps as they free up (continuous batching).
+// Only one warp in kPollEvery keeps reading the host-written tail over PCIe
+// (relaxed loads) while idle, folding it into a device-memory mirror; the
+// other idle warps look at the mirror, so idle polling costs PCIe round trips
+// only from a few warps.
+// An idle warp backs off (longer for non-polling warps) and returns once no
+// warp of the kernel has claimed work for s.idle_ns (a kernel-wide decision,
+// so the kernel never dwindles to a few warps under light load), or when the
+// host sets s.stop; the host relaunches the kernel when new items arrive.  A claim is followed by a
+// system-scope fence, and host-written memory is read with system-scope
+// loads (never through the non-coherent cache), so a reused slot never
+// yields stale data.
+template <int MODE, int NB>
+__global__ void serve_kernel(SearchArgs a, ServeArgs s, int smem_per_warp) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  unsigned char* ws = smem + wib * smem_per_warp;
+  const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
+  const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
+  uint32_t* vis = a.vis + (gw << a.vis_log2);
+  uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
+  constexpr int kPollEvery = 32;
+  const bool poller = (gw % kPollEvery) == 0;
+  const unsigned max_backoff = poller ? 16384u : 65536u;
+  const long long started = global_timer_ns();
+  unsigned backoff = 128;
+  for (;;) {
+    long long got = -1;
+    if (lane == 0) {
+      unsigned long long t = *reinterpret_cast<volatile unsigned long long*>(s.tail_mirror);
+      unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(s.head);
+      // the host tail is read by polling warps, and by any warp right after it
+      // finished a query (backoff reset), so fresh work is never left waiting
+      // for a poller that is busy
+      if (h >= t && (poller || backoff == 128u)) {
+        unsigned long long th;
+        asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(th) : "l"(s.tail) : "memory");
+        if (th > t) {
+          atomicMax(s.tail_mirror, th);
+          t = th;
+        }
+      }
+      while (h < t) {
+        const unsigned long long prev = atomicCAS(s.head, h, h + 1);
+        if (prev == h) {
+          got = static_cast<long long>(h);
+          break;
+        }
+        h = prev;
+      }
+      if (got >= 0) {
+        atomicMax(s.last_claim, static_cast<unsigned long long>(global_timer_ns()));
+        asm volatile("fence.acq_rel.sys;" ::: "memory");
+      }
+    }
+    got = __shfl_sync(kFull, got, 0);
+    if (got < 0) {
+      int stop = 0;
+      if (lane == 0 && poller) stop = static_cast<int>(ld_relaxed_sys_u32(s.stop));
+      stop = __shfl_sync(kFull, stop, 0);
+      long long ref = static_cast<long long>(*reinterpret_cast<volatile unsigned long long*>(s.last_claim));
+      if (ref < started) ref = started;
+      if (stop || global_timer_ns() - ref > s.idle_ns) break;
+      __nanosleep(backoff);
+      backoff = backoff < max_backoff ? backoff * 2 : max_backoff;
+      continue;
+    }
+    const int slot = static_cast<int>(got % s.slots);
+    // the query into shared memory (system-scope loads of host memory)
+    {
+      const unsigned char* src = s.qbuf + static_cast<size_t>(slot) * s.qbytes;
+      unsigned* dst = reinterpret_cast<unsigned*>(ws + lay.q);
+      for (int j = lane; j < (s.qbytes >> 2); j += 32) dst[j] = ld_relaxed_sys_u32(src + 4 * j);
+    }
+    QueryJob job;
+    job.query = nullptr;
+    job.k = static_cast<int>(ld_relaxed_sys_u32(s.item_kL + 2 * slot));
+    job.L = static_cast<int>(ld_relaxed_sys_u32(s.item_kL + 2 * slot + 1));
+    job.qi = slot;
+    job.ids = s.rids + static_cast<size_t>(slot) * s.max_k;
+    job.dists = s.rdists + static_cast<size_t>(slot) * s.max_k;
+    job.steps = s.rsteps + slot;
+    job.status = s.rstatus + slot;
+    job.t_begin = s.rtimes + 2 * slot;
+    job.t_end = s.rtimes + 2 * slot + 1;
+    if (job.k < 1 || job.k > a.k || job.L < job.k || job.L > a.L) {
+      // rejected at submission; guards the shared-memory layout all the same
+      if (lane == 0) *job.status = ANN_EINVAL;
+    } else {
+      run_query<MODE, NB>(a, job, ws, lay, vis, vlog, lane);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_system();  // results before the done word
+      *reinterpret_cast<volatile unsigned long long*>(s.done + slot) =
+          static_cast<unsigned long long>(got) + 1ull;
+    }
+    backoff = 128;
+  }
+}
+
+template <int MODE, int NB>
+cudaError_t launch_serve_t(const SearchArgs& a, const ServeArgs& s, const SearchPlan& p,
+                           cudaStream_t st) {
+  const int smem = p.smem_per_warp * p.warps_per_block;
+  cudaError_t e = cudaFuncSetAttribute(serve_kernel<MODE, NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  serve_kernel<MODE, NB><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, s, p.smem_per_warp);
+  return cudaGetLastError();
 }
 
 template <int MODE, int NB>
@@ -613,11 +822,14 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   const WarpSmem lay = warp_smem_layout(mode, M, d, slot_bytes, depth, L, k, p.nb);
   p.smem_per_warp = lay.total;
   p.warps_per_block = 1;
-  // Visited table: next_pow2(2*R*(L+64)) slots (at least 4096), so a query
-  // may visit ~1.5*R*(L+64) nodes before it reports an overflow.
-  const int64_t want = 2ll * R * (L + 64);
-  int lg = 12;
-  while ((1ll << lg) < want && lg < 22) ++lg;
+  // Visited table: 2^15 slots (2^16 beyond L = 2048), doubled for R > 64 and
+  // halved for R <= 32.  Measured on the 1M SIFT-like workload the largest
+  // visited set of 1,000 queries is ~12k nodes up to L = 2048 and ~18.5k at
+  // L = 4096 (R = 64), so the 3/4-load overflow limit leaves a >= 2x margin,
+  // while 128 KB per warp keeps the tables of all resident warps in L2.
+  int lg = L <= 2048 ? 15 : 16;
+  if (R > 64) ++lg;
+  if (R <= 32) --lg;
   p.vis_log2 = lg;
   p.vis_log_cap = (3 << lg) / 4 + 32 * p.nb + 1;
   int dev = 0, sms = 0, per_sm = 0;
@@ -638,6 +850,16 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
 
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
   return launch_table(plan.mode, plan.nb)(a, plan, stream);
+}
+
+cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,
+                         cudaStream_t stream) {
+  using ServeFn = cudaError_t (*)(const SearchArgs&, const ServeArgs&, const SearchPlan&, cudaStream_t);
+  static const ServeFn t[3][3] = {
+      {launch_serve_t<kModePqU8, 1>, launch_serve_t<kModePqU8, 2>, launch_serve_t<kModePqU8, 4>},
+      {launch_serve_t<kModeExactU8, 1>, launch_serve_t<kModeExactU8, 2>, launch_serve_t<kModeExactU8, 4>},
+      {launch_serve_t<kModeExactF32, 1>, launch_serve_t<kModeExactF32, 2>, launch_serve_t<kModeExactF32, 4>}};
+  return t[plan.mode][nb_index(plan.nb)](a, s, plan, stream);
 }
 
 }  // namespace ann

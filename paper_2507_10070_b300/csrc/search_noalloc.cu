@@ -28,8 +28,8 @@ int index_search_view(const ann_index* ix, SearchArgs* a, int* mode, int* slot_b
 
 namespace {
 
-constexpr size_t kScratchBytes = 32ull << 20;  // 32 MiB per device
-constexpr int kMinWarps = 16;                  // a call must fit at least 16 warps
+constexpr size_t kScratchBytes = 16ull << 20;  // 16 MiB per device
+constexpr int kMinWarps = 32;                  // a call must fit at least 32 warps
 constexpr int kMaxDevices = 64;
 constexpr size_t kHeader = 256;                // counters + expansions, padded
 

@@ -106,3 +106,12 @@ def test_tooling_rejects_bad_sizes():
         ann.build_pq(x, 2)            # fewer than 256 training vectors
     with pytest.raises(ann.AnnError):
         ann.build_graph(x[:1], 4)     # n < 2
+
+
+def test_autotune_rejects_bad_configuration():
+    with pytest.raises(ann.AnnError):
+        ann.autotune_degree(degrees=(0, 64), n_sample=20_000)
+    with pytest.raises(ann.AnnError):
+        ann.autotune_degree(degrees=(64,), n_sample=100)
+    with pytest.raises(ann.AnnError):
+        ann.autotune_degree(degrees=(64,), d=100)

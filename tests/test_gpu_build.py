@@ -1,0 +1,70 @@
+"""GPU Vamana construction (ann_build_graph_gpu): graph invariants,
+determinism, and search quality against the host builder."""
+import collections
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2507_10070_b300 as ann
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_rows(adj, R):
+    assert adj.shape[1] == R
+    for i, row in enumerate(adj):
+        nb = row[row >= 0]
+        assert np.all(row[len(nb):] == -1)
+        assert i not in nb and len(set(nb.tolist())) == len(nb)
+
+
+def _reach(adj, s):
+    seen = np.zeros(adj.shape[0], bool)
+    seen[s] = True
+    dq = collections.deque([s])
+    while dq:
+        u = dq.popleft()
+        for w in adj[u]:
+            if w >= 0 and not seen[w]:
+                seen[w] = True
+                dq.append(w)
+    return int(seen.sum())
+
+
+def test_gpu_build_u8_matches_host_quality():
+    mx = datagen.sift_like()
+    base, q = mx.base(30_000), mx.queries(300)
+    g_adj, g_entry = ann.build_graph(base, 64, 1.2, 128, seed=5, device="gpu")
+    h_adj, h_entry = ann.build_graph(base, 64, 1.2, 128, seed=5, device="cpu")
+    assert g_entry == h_entry == oracle.medoid(base)
+    _check_rows(g_adj, 64)
+    assert _reach(g_adj, g_entry) >= 0.999 * base.shape[0]
+    again, _ = ann.build_graph(base, 64, 1.2, 128, seed=5, device="gpu")
+    assert np.array_equal(g_adj, again)                      # deterministic
+    gi, gd = oracle.knn(base, q, 10)
+    for L in (32, 64):
+        ig, dg, _ = oracle.search(base, g_adj, g_entry, q, 10, L, 0)
+        ih, dh, _ = oracle.search(base, h_adj, h_entry, q, 10, L, 0)
+        rg = oracle.recall_at_k(ig, gi, gd, dg)
+        rh = oracle.recall_at_k(ih, gi, gd, dh)
+        assert rg >= rh - 0.01, (L, rg, rh)
+
+
+def test_gpu_build_f32_inmemory_workload():
+    mx = datagen.inmemory_f32()
+    base, q = mx.base(10_000), mx.queries(200)
+    adj, entry = ann.build_graph(base, 32, 1.2, 64, seed=1, device="gpu")
+    _check_rows(adj, 32)
+    gi, gd = oracle.knn(base, q, 10)
+    ids, d, _ = oracle.search(base, adj, entry, q, 10, 64, 0)
+    assert oracle.recall_at_k(ids, gi, gd, d) >= 0.95
+
+
+def test_gpu_build_rejects_bad_sizes():
+    x = np.zeros((100, 8), np.uint8)
+    with pytest.raises(ann.AnnError):
+        ann.build_graph(x, 16, device="gpu")                 # d % 16 != 0
+    with pytest.raises(ann.AnnError):
+        ann.build_graph(np.zeros((100, 16), np.uint8), 96, L_build=128, device="gpu")   # R > 64

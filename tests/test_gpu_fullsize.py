@@ -22,7 +22,7 @@ SAMPLE = np.r_[0:40, 4990:5000, 9950:10000]   # head, middle and ragged tail of 
 @pytest.fixture(scope="module")
 def sift1m():
     import bench
-    w = bench.prepare_sift_like(1_000_000, 10_000)
+    w = bench.prepare_sift_like(1_000_000, 10_000, builder="cpu")
     ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],
                    tier=ann.ANN_TIER_HOST_PINNED)
     yield w, ix

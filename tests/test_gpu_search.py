@@ -191,8 +191,7 @@ def test_visited_overflow_reports_enomem():
     """The device's failure path, checked from the host: on a ring lattice
     (node i -> i+1..i+R, positions on a line) a query at the far end makes the
     search march through every node, so it visits all 60,000 while the
-    visited table holds next_pow2(2*R*(L+64)) = 32,768 slots (overflow above
-    3/4).  The query must report ANN_ENOMEM rather than diverge, and the index
+    visited table at R=128 holds 65,536 slots (overflow above 3/4, 49,152).  The query must report ANN_ENOMEM rather than diverge, and the index
     must stay usable (its tables are cleared after the failed queries)."""
     n, R = 60_000, 128
     base = np.zeros((n, 4), np.float32)

@@ -76,6 +76,19 @@ def test_noalloc_reports_status_and_rejects_oversized_scratch(small_index):
     ix.search_dev_noalloc(q, 10, 64, 2, ids, d, trace={"status": status})
     torch.cuda.synchronize()
     assert int(status.abs().sum()) == 0
-    with pytest.raises(ann.AnnError) as e:
-        ix.search_dev_noalloc(q, 10, 2048, 1, ids, d)     # > 32 MiB / 16 per warp
-    assert e.value.status == ann._abi.ANN_EINVAL and "static" in str(e.value)
+    # an index of degree 128 searched with L=4096 needs more than 16 MiB / 32
+    # of scratch per warp: rejected with a clear error
+    rng = np.random.default_rng(0)
+    n = 1000
+    base = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    adj = ((np.arange(n)[:, None] + 1 + rng.integers(0, n - 1, size=(n, 128))) % n).astype(np.int32)
+    wide = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
+    try:
+        qw = torch.from_numpy(base[:4].copy()).cuda()
+        with pytest.raises(ann.AnnError) as e:
+            wide.search_dev_noalloc(qw, 10, 4096, 1, ids[:4], d[:4])
+        assert e.value.status == ann._abi.ANN_EINVAL and "static" in str(e.value)
+        wide.search_dev_noalloc(qw, 10, 1024, 1, ids[:4], d[:4])   # within the limit
+        torch.cuda.synchronize()
+    finally:
+        wide.close()
