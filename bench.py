@@ -292,6 +292,13 @@ def run_ours(args, rank: int, world: int):
         "setup_s": round(setup_s, 1),
         "index": {"builder": args.builder, "seconds_incl_pq_and_data": round(index_build_s, 1)},
     }
+    if args.autotune:
+        t_at = time.time()
+        out["autotune"] = ann.autotune_degree(degrees=(32, 48, 64, 96), n_sample=100_000, d=128,
+                                              M=32, L=32, nq=4096, seed=1)
+        out["autotune"]["seconds"] = round(time.time() - t_at, 1)
+        out["autotune"]["what"] = ("computation / I/O balanced degree selector on random-link "
+                                   "100k-node sample indices (ann_autotune_degree)")
     if args.serve_seconds > 0:
         out["serving"] = run_serving(ix, w, gt_ids, gt_d, chosen_L, best_depth, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
@@ -466,6 +473,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the serving (request loop) measurement; 0 skips it")
+    ap.add_argument("--autotune", type=int, default=1, help="run the degree selector (1) or not (0)")
     ap.add_argument("--builder", choices=["cpu", "gpu"], default="gpu",
                     help="Vamana construction for the index (off the clock)")
     ap.add_argument("--probe-sweep", action="store_true",

@@ -44,6 +44,13 @@ typedef enum {
 
 typedef enum { ANN_U8 = 0, ANN_F32 = 1 } ann_dtype;
 
+/* How navigation distances are computed (ann_graph_desc.nav). */
+typedef enum {
+  ANN_NAV_AUTO = 0, /* PQ codes if M > 0, otherwise the vectors themselves */
+  ANN_NAV_BF16 = 1, /* BF16 copies of float32 vectors, FP32 accumulation */
+  ANN_NAV_FP8 = 2   /* FP8-E4M3 copies of float32 vectors * nav_scale, FP32 accumulation */
+} ann_nav;
+
 /* Where the node blocks (full vector + adjacency) live. */
 typedef enum {
   ANN_TIER_HOST_PINNED = 0, /* host pinned memory read by the GPU over PCIe (default) */
@@ -63,6 +70,11 @@ typedef struct ann_index ann_index; /* opaque, owned by the library */
  *    to `tier`; codes and codebook go to HBM.
  *  - M == 0: exact navigation; vectors and adjacency go to HBM (tier must be
  *    ANN_TIER_HBM).  dtype ANN_U8 or ANN_F32, d % 4 == 0.
+ *  - Precision variants (dtype ANN_F32, tier ANN_TIER_HBM): navigation on
+ *    compressed copies -- nav = ANN_NAV_BF16 or ANN_NAV_FP8 with M == 0, or
+ *    float PQ with M > 0 (M % 16 == 0, M <= 64, d % M == 0, any float
+ *    codebook) -- followed by an exact FP32 rerank of the top
+ *    rerank_mult * k expanded candidates (at most 256, at most L).
  * Limits: 1 <= n < 2^31, 4 <= d <= 512, 1 <= R <= 128, 0 <= entry < n; every
  * adjacency id is -1 or in [0, n) and a row ends at its first -1.
  */
@@ -78,6 +90,9 @@ typedef struct {
   const float* codebook; /* M*256*(d/M): centroid c of subspace m at (m*256+c)*(d/M) */
   const uint8_t* codes;  /* n*M PQ codes */
   int32_t tier;          /* ann_tier of the node blocks */
+  int32_t nav;           /* ann_nav (0 = ANN_NAV_AUTO) */
+  float nav_scale;       /* ANN_NAV_FP8: values are encoded as x * nav_scale (> 0) */
+  int32_t rerank_mult;   /* precision variants: rerank the top rerank_mult*k (0 means 4) */
 } ann_graph_desc;
 
 /* Per-query outputs of a search (each pointer may be NULL).  Memory kind as
@@ -342,6 +357,19 @@ int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
 int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
                         float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
                         int32_t* entry_out);
+
+/*
+ * Compressed navigation vectors (host-side encoders).  The precision
+ * workload compares navigation on BF16 and FP8-E4M3 copies of float32
+ * vectors with float32 navigation.
+ *  ann_encode_bf16: the upper 16 bits of each float32, rounded to nearest,
+ *    ties to even.
+ *  ann_encode_fp8e4m3: x*scale in FP8-E4M3 (OCP 8-bit float, E4M3: bias 7,
+ *    largest finite 448, no infinities, S.1111.111 = NaN), rounded to
+ *    nearest, ties to even, finite values beyond 448 saturated to +-448.
+ */
+int ann_encode_bf16(const float* x, int64_t n, uint16_t* out);
+int ann_encode_fp8e4m3(const float* x, int64_t n, float scale, uint8_t* out);
 
 /*
  * Exact k nearest neighbours by brute force on the GPU (ground truth).

@@ -61,7 +61,7 @@ def _load():
         lib.orc_pq_encode.argtypes = [I, P, I64, I, I, I, P, P]
         lib.orc_search.restype = I
         lib.orc_search.argtypes = [I, P, I64, I, I, P, I, P, P, ctypes.c_int32, P, I64,
-                                   I, I, I, P, P, P, P, I, P, I]
+                                   I, I, I, P, P, P, P, I, P, P, I, I]
         lib.orc_vamana.restype = I
         lib.orc_vamana.argtypes = [I, P, I64, I, I, D, I, ctypes.c_int32, P, P, I, P]
         _lib = lib
@@ -140,7 +140,8 @@ def pq_encode(base: np.ndarray, codebook: np.ndarray) -> np.ndarray:
 def search(base: np.ndarray, adj: np.ndarray, entry: int, queries: np.ndarray, k: int,
            L: int, depth: int, codebook: np.ndarray | None = None,
            codes: np.ndarray | None = None, threads: int | None = None,
-           trace_cap: int = 0, return_visited: bool = False):
+           trace_cap: int = 0, return_visited: bool = False,
+           nav_vectors: np.ndarray | None = None, rerank: int = 0):
     """Best-first search with relaxed fetch depth `depth` (0 = synchronous).
 
     Navigation uses PQ codes when `codebook`/`codes` are given, exact
@@ -148,6 +149,10 @@ def search(base: np.ndarray, adj: np.ndarray, entry: int, queries: np.ndarray, k
     steps int32 (nq,)) and, with trace_cap > 0, the expansion sequences
     (nq, trace_cap) padded with -1; with return_visited, also the number of
     distinct nodes each query inserted into its visited set (last element).
+    `nav_vectors` (n x d, float64): navigate on these instead of the base or
+    the codes.  `rerank` > 0: the result is the exact rerank of the `rerank`
+    expanded nodes nearest by navigation distance (instead of all expanded
+    nodes ranked exactly).
     """
     base = _c(base)
     adj = _c(adj, np.int32)
@@ -165,10 +170,13 @@ def search(base: np.ndarray, adj: np.ndarray, entry: int, queries: np.ndarray, k
     steps = np.empty(nq, np.int32)
     trace = np.full((nq, trace_cap), -1, np.int32) if trace_cap else None
     nvis = np.empty(nq, np.int32) if return_visited else None
+    navv = None if nav_vectors is None else _c(nav_vectors, np.float64)
+    if navv is not None:
+        assert navv.shape == (n, d)
     rc = _load().orc_search(_dtype_code(base), _ptr(base), n, d, adj.shape[1], _ptr(adj), M,
                             _ptr(codebook), _ptr(codes), entry, _ptr(queries), nq, k, L, depth,
                             _ptr(ids), _ptr(dists), _ptr(steps), _ptr(trace), trace_cap,
-                            _ptr(nvis), threads or default_threads())
+                            _ptr(nvis), _ptr(navv), int(rerank), threads or default_threads())
     if rc != 0:
         raise ValueError("oracle search: invalid arguments")
     out = (ids, dists, steps) + ((trace,) if trace_cap else ())
@@ -188,6 +196,25 @@ def vamana(base: np.ndarray, R: int, alpha: float, L_build: int, entry: int,
     if rc != 0:
         raise ValueError("oracle vamana: invalid arguments")
     return adj
+
+
+def decode_bf16(bits: np.ndarray) -> np.ndarray:
+    """BF16 bit patterns -> float64 (the value is the float32 with these upper 16 bits)."""
+    b = np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)
+    return b.view(np.float32).astype(np.float64)
+
+
+def decode_fp8e4m3(b: np.ndarray, scale: float = 1.0) -> np.ndarray:
+    """FP8-E4M3 bytes -> float64 values / scale, from the format's definition:
+    sign bit, 4-bit exponent with bias 7, 3-bit mantissa; exponent field 0 is
+    subnormal (m * 2^-9); S.1111.111 is NaN; no infinities."""
+    b = np.asarray(b, np.uint8).astype(np.int64)
+    s = np.where(b & 0x80, -1.0, 1.0)
+    e = (b >> 3) & 0xF
+    m = b & 0x7
+    val = np.where(e == 0, m * 2.0 ** -9, (1.0 + m / 8.0) * np.exp2(e - 7.0))
+    val = np.where((e == 15) & (m == 7), np.nan, val)
+    return s * val / scale
 
 
 def recall_at_k(ids, gt_ids, gt_dists, res_dists, k: int = 10) -> float:

@@ -371,12 +371,22 @@ typedef struct {
   const float* codebook;
   const uint8_t* codes;
   int32_t entry;
+  const double* navv;  /* n x d navigation vectors (float64), or NULL */
+  int rerank;          /* > 0: results = exact rerank of the `rerank` expanded nodes nearest by nav */
 } index_t;
 
 /* Navigation distance of node w: the squared distance between the query and
  * w's vector as the navigating representation stores it -- the decoded PQ
  * reconstruction when M > 0, the full-precision vector otherwise. */
 static double nav_dist(const index_t* ix, const void* q, int32_t w) {
+  if (ix->navv) {
+    double s = 0.0;
+    for (int j = 0; j < ix->d; ++j) {
+      double t = elem(ix->dtype, q, j) - ix->navv[(int64_t)w * ix->d + j];
+      s += t * t;
+    }
+    return s;
+  }
   if (ix->M == 0) return dist_row(ix->dtype, ix->base, w, q, ix->d);
   int dsub = ix->d / ix->M;
   double s = 0.0;
@@ -448,7 +458,8 @@ static int search_one(const index_t* ix, const void* q, int k, int L, int D,
         *results_cap *= 2;
         *results = (pair_t*)realloc(*results, sizeof(pair_t) * (*results_cap));
       }
-      (*results)[nres].dist = dist_row(ix->dtype, ix->base, u, q, ix->d);
+      /* with a rerank, the result set first ranks expanded nodes by navigation */
+      (*results)[nres].dist = ix->rerank > 0 ? nav_dist(ix, q, u) : dist_row(ix->dtype, ix->base, u, q, ix->d);
       (*results)[nres].id = u;
       ++nres;
       const int32_t* nb = ix->adj + (int64_t)u * ix->R;
@@ -476,6 +487,13 @@ static int search_one(const index_t* ix, const void* q, int k, int L, int D,
     }
   }
   qsort(*results, (size_t)nres, sizeof(pair_t), pair_cmp);
+  if (ix->rerank > 0) {
+    /* exact distances of the `rerank` best by navigation, ranked again */
+    if (nres > ix->rerank) nres = ix->rerank;
+    for (int64_t i = 0; i < nres; ++i)
+      (*results)[i].dist = dist_row(ix->dtype, ix->base, (*results)[i].id, q, ix->d);
+    qsort(*results, (size_t)nres, sizeof(pair_t), pair_cmp);
+  }
   if (nvisited_out) *nvisited_out = nvisited;
   for (int j = 0; j < k; ++j) {
     ids_out[j] = j < nres ? (*results)[j].id : -1;
@@ -522,10 +540,10 @@ int orc_search(int dtype, const void* base, int64_t n, int d, int R, const int32
                int M, const float* codebook, const uint8_t* codes, int32_t entry,
                const void* queries, int64_t nq, int k, int L, int D, int32_t* ids,
                double* dists, int32_t* steps, int32_t* expanded, int expanded_cap,
-               int32_t* nvisited, int nthreads) {
+               int32_t* nvisited, const double* navv, int rerank, int nthreads) {
   if (k < 1 || L < k || D < 0 || n < 1 || entry < 0 || entry >= n) return -1;
   if (M > 0 && d % M != 0) return -1;
-  index_t ix = {dtype, base, n, d, R, adj, M, codebook, codes, entry};
+  index_t ix = {dtype, base, n, d, R, adj, M, codebook, codes, entry, navv, rerank};
   search_ctx c = {&ix, queries, k, L, D, ids, dists, steps, expanded, expanded_cap, nvisited};
   parallel_for(nq, nthreads, search_range, &c);
   return 0;

@@ -16,8 +16,8 @@ import os
 import numpy as np
 
 from . import _abi
-from ._abi import (ANN_F32, ANN_TIER_HBM, ANN_TIER_HOST_PINNED, ANN_U8, AnnError,
-                   GraphDesc, SearchStats, Trace)
+from ._abi import (ANN_F32, ANN_NAV_AUTO, ANN_NAV_BF16, ANN_NAV_FP8, ANN_TIER_HBM,
+                   ANN_TIER_HOST_PINNED, ANN_U8, AnnError, GraphDesc, SearchStats, Trace)
 
 __all__ = ["Index", "Server", "AnnError", "build_pq", "build_graph", "knn_exact", "probe_read_bandwidth",
            "autotune_degree",
@@ -54,7 +54,7 @@ def _p(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def _desc(vectors, adj, entry, codebook, codes, tier):
+def _desc(vectors, adj, entry, codebook, codes, tier, nav=0, nav_scale=0.0, rerank_mult=0):
     vectors = _c(vectors)
     adj = _c(adj, np.int32)
     n, d = vectors.shape
@@ -67,7 +67,8 @@ def _desc(vectors, adj, entry, codebook, codes, tier):
     keep = (vectors, adj, codebook, codes)
     desc = GraphDesc(n=n, d=d, dtype=_dtype_code(vectors), R=adj.shape[1], entry=int(entry),
                      vectors=_p(vectors), adj=_p(adj), M=M, codebook=_p(codebook),
-                     codes=_p(codes), tier=tier)
+                     codes=_p(codes), tier=tier, nav=nav, nav_scale=nav_scale,
+                     rerank_mult=rerank_mult)
     return desc, keep
 
 
@@ -80,7 +81,8 @@ class Index:
     """A loaded index: node blocks in `tier`, PQ codes / vectors in HBM."""
 
     def __init__(self, vectors=None, adj=None, entry=0, codebook=None, codes=None,
-                 tier: int = ANN_TIER_HOST_PINNED, path: str | None = None):
+                 tier: int = ANN_TIER_HOST_PINNED, path: str | None = None, nav: int = 0,
+                 nav_scale: float = 0.0, rerank_mult: int = 0):
         self._h = ctypes.c_void_p()
         if path is not None:
             _check(_lib().ann_load_graph_file(ctypes.byref(self._h), path.encode(), tier))
@@ -89,7 +91,7 @@ class Index:
             fields = hdr[16:40].view(np.int32)
             self.d, self.dtype = int(fields[0]), int(fields[1])
         else:
-            desc, _ = _desc(vectors, adj, entry, codebook, codes, tier)
+            desc, _ = _desc(vectors, adj, entry, codebook, codes, tier, nav, nav_scale, rerank_mult)
             _check(_lib().ann_load_graph(ctypes.byref(self._h), ctypes.byref(desc)))
             self.d, self.dtype = desc.d, desc.dtype
         self.n = int(_lib().ann_index_size(self._h))
@@ -282,6 +284,22 @@ def autotune_degree(degrees=(32, 48, 64, 96), n_sample: int = 100_000, d: int = 
               "qps_sync": round(p.qps_sync, 1)} for p in pts]
     return {"table": table, "degree": best_d.value, "depth": best_depth.value,
             "qps_by_depth": [round(float(x), 1) for x in qps], "warps_per_query": 1}
+
+
+def encode_bf16(x):
+    """float32 -> BF16 bit patterns (uint16), round to nearest even."""
+    x = _c(x, np.float32)
+    out = np.empty(x.shape, np.uint16)
+    _check(_lib().ann_encode_bf16(_p(x), x.size, _p(out)))
+    return out
+
+
+def encode_fp8e4m3(x, scale: float = 1.0):
+    """float32 * scale -> FP8-E4M3 bytes (uint8), round to nearest even, saturating."""
+    x = _c(x, np.float32)
+    out = np.empty(x.shape, np.uint8)
+    _check(_lib().ann_encode_fp8e4m3(_p(x), x.size, ctypes.c_float(scale), _p(out)))
+    return out
 
 
 def knn_exact(base, queries, k: int):

@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(PKG, "libann.so")
 ANN_OK, ANN_EINVAL, ANN_ENOMEM, ANN_ECUDA, ANN_ETIMEOUT, ANN_EBUSY, ANN_EIO = 0, -1, -2, -3, -4, -5, -6
 ANN_U8, ANN_F32 = 0, 1
 ANN_TIER_HOST_PINNED, ANN_TIER_HBM = 0, 1
+ANN_NAV_AUTO, ANN_NAV_BF16, ANN_NAV_FP8 = 0, 1, 2
 
 STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA",
                 -4: "ANN_ETIMEOUT", -5: "ANN_EBUSY", -6: "ANN_EIO"}
@@ -21,7 +22,7 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
-           "ann_autotune_degree", "ann_build_graph_gpu"]
+           "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3"]
 
 
 class AnnError(RuntimeError):
@@ -34,7 +35,8 @@ class GraphDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("R", ctypes.c_int32), ("entry", ctypes.c_int32), ("vectors", ctypes.c_void_p),
                 ("adj", ctypes.c_void_p), ("M", ctypes.c_int32), ("codebook", ctypes.c_void_p),
-                ("codes", ctypes.c_void_p), ("tier", ctypes.c_int32)]
+                ("codes", ctypes.c_void_p), ("tier", ctypes.c_int32), ("nav", ctypes.c_int32),
+                ("nav_scale", ctypes.c_float), ("rerank_mult", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -122,6 +124,10 @@ def lib():
         L.ann_build_graph_gpu.restype = ctypes.c_int
         L.ann_build_graph_gpu.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, P,
                                           ctypes.POINTER(ctypes.c_int32)]
+        L.ann_encode_bf16.restype = ctypes.c_int
+        L.ann_encode_bf16.argtypes = [P, I64, P]
+        L.ann_encode_fp8e4m3.restype = ctypes.c_int
+        L.ann_encode_fp8e4m3.argtypes = [P, I64, ctypes.c_float, P]
         L.ann_knn_exact.restype = ctypes.c_int
         L.ann_knn_exact.argtypes = [P, I32, I64, I32, P, I64, I32, P, P]
         L.ann_probe_read_bandwidth.restype = ctypes.c_int

@@ -15,8 +15,18 @@ namespace ann {
 enum Mode : int {
   kModePqU8 = 0,     // PQ navigation, node blocks in the storage tier (uint8 data)
   kModeExactU8 = 1,  // exact navigation on uint8 vectors in HBM
-  kModeExactF32 = 2  // exact navigation on float32 vectors in HBM
+  kModeExactF32 = 2, // exact navigation on float32 vectors in HBM
+  kModeBF16 = 3,     // navigation on BF16 copies of float32 vectors (HBM), FP32 accumulation
+  kModeFP8 = 4,      // navigation on FP8-E4M3 copies (x * scale), FP32 accumulation
+  kModePqF32 = 5,    // PQ navigation with a float codebook (float32 data), FP32 lookup table
+  kNumModes = 6
 };
+
+// Modes whose query and distances are float32 (keys hold float bit patterns).
+__host__ __device__ constexpr bool mode_f32(int m) {
+  return m == kModeExactF32 || m == kModeBF16 || m == kModeFP8 || m == kModePqF32;
+}
+__host__ __device__ constexpr bool mode_pq(int m) { return m == kModePqU8 || m == kModePqF32; }
 
 constexpr int kMaxL = 4096;
 constexpr int kMaxDepth = 4;
@@ -35,6 +45,9 @@ struct SearchArgs {
   int32_t slot_bytes;       // bytes fetched per expansion into a ring slot (multiple of 16)
   const uint8_t* codes;     // PQ mode: n*M codes (HBM)
   const uint32_t* cb_words; // PQ mode: M*256*(dsub/4) words, 4 uint8 coordinates each
+  const float* cb_f32;      // float PQ mode: M*256*dsub centroid coordinates
+  const void* nav;          // BF16 / FP8 modes: n*d navigation copies (HBM)
+  float nav_inv_scale;      // FP8 mode: 1 / the encoding scale
   const void* vectors;      // exact modes: n*d elements (HBM)
   const int32_t* adj;       // exact modes: n*adj_stride ids (HBM)
   int32_t adj_stride;       // ids per adjacency row (multiple of 4)
@@ -100,13 +113,13 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
   WarpSmem s;
   int off = 0;
   s.lut = off;
-  off += (mode == kModePqU8) ? M * 256 * 4 : 0;
+  off += mode_pq(mode) ? M * 256 * 4 : 0;
   off = align_up(off, 16);
   s.ring = off;
   off += (depth + 1) * slot_bytes;
   off = align_up(off, 16);
   s.q = off;
-  off += (mode == kModeExactF32) ? d * 4 : d;
+  off += mode_f32(mode) ? d * 4 : d;
   off = align_up(off, 16);
   s.keys = off;
   off += L * 8;
@@ -131,6 +144,10 @@ cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStrea
 // Persistent serving kernel (a.L / a.k are the largest L / k it accepts).
 cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,
                          cudaStream_t stream);
+
+// Exact FP32 rerank of kc candidates per query down to k (kc <= 256).
+cudaError_t launch_rerank(const float* vectors, int d, const float* queries, int nq, const int32_t* cand,
+                          int kc, int k, int32_t* ids, float* dists, cudaStream_t st);
 
 // Storage-tier read probe kernel launcher.
 cudaError_t launch_read_probe(const uint8_t* region, int64_t nblocks, int block_bytes, int iters,

@@ -9,9 +9,9 @@
 //  1. gather the batch's vectors;
 //  2. GreedySearch(entry, x_p, L_build) for all of them at once with the
 //     library's search kernel (exact navigation on the vectors in HBM,
-//     depth 0); the L_build expanded nodes nearest to x_p form the candidate
-//     pool (DiskANN uses the whole expanded set, which is these plus the few
-//     expanded nodes that fell below them);
+//     depth 0); the expanded nodes nearest to x_p, up to L_build + 64 (at
+//     most 256 - R), form the candidate pool -- in practice the whole
+//     expanded set, as in DiskANN;
 //  3. RobustPrune(p, pool u N(p)) -- one warp per node (prune_kernel);
 //  4. back edges j <- p: the (j, p) pairs are sorted on the device (CUB
 //     radix sort), grouped by j, and each target appends its new sources or,
@@ -314,8 +314,9 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
 
   const int64_t max_batch = std::max<int64_t>(1, n / 50);
   const int mode = dtype == ANN_U8 ? kModeExactU8 : kModeExactF32;
+  const int pool = std::min(L_build + 64, kCandMax - R);  // results kept per search
   SearchPlan plan;
-  cudaError_t e = plan_search(mode, R, 0, d, stride * 4, 0, L_build, L_build, max_batch, &plan);
+  cudaError_t e = plan_search(mode, R, 0, d, stride * 4, 0, L_build, pool, max_batch, &plan);
   if (e != cudaSuccess) return cuda_error(e, "plan build search");
   const size_t nwarps = (size_t)plan.blocks * plan.warps_per_block;
   uint8_t *base_d = nullptr, *qbuf = nullptr;
@@ -351,8 +352,8 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   GB_TRY(dmalloc(&order_d, (size_t)n), "cudaMalloc order");
   GB_TRY(cudaMemcpy(order_d, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice), "upload order");
   GB_TRY(dmalloc(&qbuf, (size_t)max_batch * row_bytes), "cudaMalloc batch");
-  GB_TRY(dmalloc(&cand_ids, (size_t)max_batch * L_build), "cudaMalloc candidates");
-  GB_TRY(dmalloc(&cand_d, (size_t)max_batch * L_build), "cudaMalloc candidates");
+  GB_TRY(dmalloc(&cand_ids, (size_t)max_batch * pool), "cudaMalloc candidates");
+  GB_TRY(dmalloc(&cand_d, (size_t)max_batch * pool), "cudaMalloc candidates");
   GB_TRY(dmalloc(&vis, nwarps << plan.vis_log2), "cudaMalloc visited");
   GB_TRY(cudaMemset(vis, 0, (nwarps << plan.vis_log2) * 4), "cudaMemset");
   GB_TRY(dmalloc(&vlog, nwarps * plan.vis_log_cap), "cudaMalloc visited log");
@@ -388,7 +389,7 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   a.slot_bytes = stride * 4;
   a.block_bytes = stride * 4;
   a.queries = qbuf;
-  a.k = L_build;
+  a.k = pool;  // more results than list entries: every expanded node, not only the L best
   a.L = L_build;
   a.depth = 0;
   a.ids = cand_ids;
@@ -414,7 +415,7 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
       a.nq = b;
       GB_TRY(launch_search(a, pb, st), "build search");
       // forward prune: pool = the search results, plus the current row
-      fill_pool_meta<<<(b + 255) / 256, 256, 0, st>>>(b, L_build, off, cnt);
+      fill_pool_meta<<<(b + 255) / 256, 256, 0, st>>>(b, pool, off, cnt);
       if (dtype == ANN_U8)
         prune_kernel<true><<<(b + 3) / 4, 128, 0, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, b, 1, 0, adj_d, stride);
       else

@@ -72,6 +72,11 @@ struct ann_index {
   bool blocks_in_hbm = false;
   uint8_t* codes = nullptr;
   uint32_t* cb_words = nullptr;
+  float* cb_f32 = nullptr;   // float PQ codebook (precision variant)
+  void* nav = nullptr;       // BF16 / FP8 navigation copies
+  float nav_inv_scale = 1.f;
+  int rerank_mult = 4;
+  DevBuf rr_ids, rr_d;       // candidates before the exact rerank
   void* vectors = nullptr;
   int32_t* adj = nullptr;
   // scratch
@@ -98,6 +103,10 @@ void release(ann_index* ix) {
   if (ix->blocks_in_hbm && ix->blocks_dev) cudaFree(ix->blocks_dev);
   cudaFree(ix->codes);
   cudaFree(ix->cb_words);
+  cudaFree(ix->cb_f32);
+  cudaFree(ix->nav);
+  ix->rr_ids.release();
+  ix->rr_d.release();
   cudaFree(ix->vectors);
   cudaFree(ix->adj);
   cudaFree(ix->vis);
@@ -122,7 +131,19 @@ int validate_desc(const ann_graph_desc* g) {
   if (!g->vectors || !g->adj) return set_error(ANN_EINVAL, "vectors and adj are required");
   if (g->tier != ANN_TIER_HOST_PINNED && g->tier != ANN_TIER_HBM) return set_error(ANN_EINVAL, "unknown tier %d", g->tier);
   if (g->M < 0) return set_error(ANN_EINVAL, "M=%d < 0", g->M);
-  if (g->M > 0) {
+  if (g->nav < ANN_NAV_AUTO || g->nav > ANN_NAV_FP8) return set_error(ANN_EINVAL, "unknown nav %d", g->nav);
+  if (g->rerank_mult < 0 || g->rerank_mult > 64) return set_error(ANN_EINVAL, "rerank_mult %d out of [0,64]", g->rerank_mult);
+  if (g->nav != ANN_NAV_AUTO) {
+    if (g->dtype != ANN_F32 || g->M != 0 || g->tier != ANN_TIER_HBM)
+      return set_error(ANN_EINVAL, "BF16 / FP8 navigation needs float32 data, M == 0 and ANN_TIER_HBM");
+    if (g->nav == ANN_NAV_FP8 && !(g->nav_scale > 0.f)) return set_error(ANN_EINVAL, "FP8 navigation needs nav_scale > 0");
+  }
+  if (g->M > 0 && g->dtype == ANN_F32) {
+    if (g->M % 16 || g->M > kMaxM || g->d % g->M)
+      return set_error(ANN_EINVAL, "float PQ needs M %% 16 == 0, M <= %d, d %% M == 0 (d=%d, M=%d)", kMaxM, g->d, g->M);
+    if (!g->codebook || !g->codes) return set_error(ANN_EINVAL, "PQ navigation needs codebook and codes");
+    if (g->tier != ANN_TIER_HBM) return set_error(ANN_EINVAL, "float PQ navigation keeps vectors in HBM: use ANN_TIER_HBM");
+  } else if (g->M > 0) {
     if (g->dtype != ANN_U8) return set_error(ANN_EINVAL, "PQ navigation needs uint8 data");
     if (g->M % 16 || g->M > kMaxM || g->d % g->M || (g->d / g->M) % 4)
       return set_error(ANN_EINVAL, "PQ needs M %% 16 == 0, M <= %d, d %% M == 0, (d/M) %% 4 == 0 (d=%d, M=%d)", kMaxM, g->d, g->M);
@@ -170,7 +191,11 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
   ix->M = g->M;
   ix->dsub = g->M > 0 ? g->d / g->M : 0;
   ix->tier = g->tier;
-  ix->mode = g->M > 0 ? kModePqU8 : (g->dtype == ANN_U8 ? kModeExactU8 : kModeExactF32);
+  if (g->M > 0) ix->mode = g->dtype == ANN_U8 ? kModePqU8 : kModePqF32;
+  else if (g->nav == ANN_NAV_BF16) ix->mode = kModeBF16;
+  else if (g->nav == ANN_NAV_FP8) ix->mode = kModeFP8;
+  else ix->mode = g->dtype == ANN_U8 ? kModeExactU8 : kModeExactF32;
+  ix->rerank_mult = g->rerank_mult > 0 ? g->rerank_mult : 4;
   const int64_t n = g->n;
   const int R = g->R, d = g->d;
   cudaError_t e;
@@ -264,6 +289,25 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
       }
     ANN_TRY(cudaMalloc(&ix->adj, rows.size() * 4), "cudaMalloc adjacency");
     ANN_TRY(cudaMemcpy(ix->adj, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice), "upload adjacency");
+    const float* fv = static_cast<const float*>(g->vectors);
+    if (ix->mode == kModeBF16) {
+      std::vector<uint16_t> b((size_t)n * d);
+      ann_encode_bf16(fv, (int64_t)b.size(), b.data());
+      ANN_TRY(cudaMalloc(&ix->nav, b.size() * 2), "cudaMalloc navigation copy");
+      ANN_TRY(cudaMemcpy(ix->nav, b.data(), b.size() * 2, cudaMemcpyHostToDevice), "upload navigation copy");
+    } else if (ix->mode == kModeFP8) {
+      std::vector<uint8_t> b((size_t)n * d);
+      ann_encode_fp8e4m3(fv, (int64_t)b.size(), g->nav_scale, b.data());
+      ix->nav_inv_scale = 1.0f / g->nav_scale;
+      ANN_TRY(cudaMalloc(&ix->nav, b.size()), "cudaMalloc navigation copy");
+      ANN_TRY(cudaMemcpy(ix->nav, b.data(), b.size(), cudaMemcpyHostToDevice), "upload navigation copy");
+    } else if (ix->mode == kModePqF32) {
+      const size_t ncb = (size_t)g->M * 256 * (d / g->M);
+      ANN_TRY(cudaMalloc(&ix->cb_f32, ncb * 4), "cudaMalloc codebook");
+      ANN_TRY(cudaMemcpy(ix->cb_f32, g->codebook, ncb * 4, cudaMemcpyHostToDevice), "upload codebook");
+      ANN_TRY(cudaMalloc(&ix->codes, (size_t)n * g->M), "cudaMalloc codes");
+      ANN_TRY(cudaMemcpy(ix->codes, g->codes, (size_t)n * g->M, cudaMemcpyHostToDevice), "upload codes");
+    }
   }
 #undef ANN_TRY
   *out = ix;
@@ -286,10 +330,26 @@ int validate_search(const ann_index* ix, const void* q, int64_t nq, int k, int L
 }
 
 // Enqueue one search of nq device-resident queries on `st`.
+bool rerank_mode(int mode) { return mode == kModeBF16 || mode == kModeFP8 || mode == kModePqF32; }
+
 int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int depth, int32_t* ids,
                    float* dists, const ann_trace* tr, cudaStream_t st, bool timed) {
   if (nq == 0) return ANN_OK;
   const int slot_bytes = ix->slot_bytes;
+  // precision variants: keep the top rerank_mult*k expanded by navigation
+  // distance, then rerank them exactly in FP32
+  const bool rr = rerank_mode(ix->mode);
+  const int k_out = k;
+  int32_t* ids_out = ids;
+  float* dists_out = dists;
+  if (rr) {
+    k = std::min(L, std::min(256, std::max(k, ix->rerank_mult * k)));
+    cudaError_t e1 = ix->rr_ids.ensure((size_t)nq * k * 4);
+    if (e1 == cudaSuccess) e1 = ix->rr_d.ensure((size_t)nq * k * 4);
+    if (e1 != cudaSuccess) return cuda_error(e1, "rerank buffers");
+    ids = static_cast<int32_t*>(ix->rr_ids.p);
+    dists = static_cast<float*>(ix->rr_d.p);
+  }
   SearchPlan plan;
   cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
@@ -328,6 +388,9 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   a.slot_bytes = ix->slot_bytes;
   a.codes = ix->codes;
   a.cb_words = ix->cb_words;
+  a.cb_f32 = ix->cb_f32;
+  a.nav = ix->nav;
+  a.nav_inv_scale = ix->nav_inv_scale;
   a.vectors = ix->vectors;
   a.adj = ix->adj;
   a.adj_stride = ix->adj_stride;
@@ -353,6 +416,11 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   if (timed) cudaEventRecord(ix->ev0, st);
   e = launch_search(a, plan, st);
   if (e != cudaSuccess) return cuda_error(e, "search kernel launch");
+  if (rr) {
+    e = launch_rerank(static_cast<const float*>(ix->vectors), ix->d, static_cast<const float*>(q), (int)nq,
+                      ids, k, k_out, ids_out, dists_out, st);
+    if (e != cudaSuccess) return cuda_error(e, "rerank kernel launch");
+  }
   if (timed) cudaEventRecord(ix->ev1, st);
   return ANN_OK;
 }
@@ -410,7 +478,7 @@ int ann_search(ann_index* ix, const void* queries, int64_t nq, int32_t k, int32_
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (nq == 0) return ANN_OK;
   cudaStream_t st = ix->stream;
-  const size_t qbytes = (size_t)nq * ix->d * elt_size(ix->dtype);
+  const size_t qbytes = (size_t)nq * ix->d * elt_size(ix->dtype);  // float32 for the precision variants
   cudaError_t e = ix->q_stage.ensure(qbytes);
   if (e == cudaSuccess) e = ix->ids_stage.ensure((size_t)nq * k * 4);
   if (e == cudaSuccess) e = ix->dists_stage.ensure((size_t)nq * k * 4);
@@ -646,6 +714,9 @@ int index_search_view(const ann_index* ix, SearchArgs* a, int* mode, int* slot_b
   a->slot_bytes = ix->slot_bytes;
   a->codes = ix->codes;
   a->cb_words = ix->cb_words;
+  a->cb_f32 = ix->cb_f32;
+  a->nav = ix->nav;
+  a->nav_inv_scale = ix->nav_inv_scale;
   a->vectors = ix->vectors;
   a->adj = ix->adj;
   a->adj_stride = ix->adj_stride;

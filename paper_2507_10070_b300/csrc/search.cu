@@ -33,6 +33,8 @@
 // The exact-navigation modes replace a1/a8 by exact distances of neighbour
 // vectors gathered from HBM, and fetch the node's adjacency row instead of a
 // node block; the result distance of an expanded node is its list distance.
+#include <cuda_fp8.h>
+
 #include <cstdint>
 
 #include "ann_internal.h"
@@ -274,6 +276,53 @@ struct QueryJob {
   int64_t* t_end;
 };
 
+// Navigation distance from a compressed copy (BF16 or FP8-E4M3 x scale) of
+// base vector w, FP32 accumulation.  BF16 -> float is the 16-bit shift;
+// FP8 -> float uses CUDA's own conversion.
+template <int MODE>
+__device__ __forceinline__ unsigned nav_dist_warp(const SearchArgs& a, const unsigned char* qs,
+                                                  int w, int lane) {
+  const float4* q = reinterpret_cast<const float4*>(qs);
+  float acc = 0.f;
+  if (MODE == kModeBF16) {
+    const uint2* x = reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(a.nav) +
+                                                    static_cast<size_t>(w) * a.d);
+    for (int j = lane; j < (a.d >> 2); j += 32) {
+      const uint2 v = __ldg(x + j);
+      const float4 qv = q[j];
+      float t;
+      t = qv.x - __uint_as_float(v.x << 16); acc = fmaf(t, t, acc);
+      t = qv.y - __uint_as_float(v.x & 0xffff0000u); acc = fmaf(t, t, acc);
+      t = qv.z - __uint_as_float(v.y << 16); acc = fmaf(t, t, acc);
+      t = qv.w - __uint_as_float(v.y & 0xffff0000u); acc = fmaf(t, t, acc);
+    }
+  } else {
+    const unsigned* x = reinterpret_cast<const unsigned*>(static_cast<const uint8_t*>(a.nav) +
+                                                          static_cast<size_t>(w) * a.d);
+    const float s = a.nav_inv_scale;
+    for (int j = lane; j < (a.d >> 2); j += 32) {
+      __nv_fp8x4_e4m3 f;
+      f.__x = __ldg(x + j);
+      const float4 xv = static_cast<float4>(f);
+      const float4 qv = q[j];
+      float t;
+      t = qv.x - xv.x * s; acc = fmaf(t, t, acc);
+      t = qv.y - xv.y * s; acc = fmaf(t, t, acc);
+      t = qv.z - xv.z * s; acc = fmaf(t, t, acc);
+      t = qv.w - xv.w * s; acc = fmaf(t, t, acc);
+    }
+  }
+  return __float_as_uint(warp_sum_f32(acc));
+}
+
+// Navigation distance of node w for the non-PQ modes.
+template <int MODE>
+__device__ __forceinline__ unsigned navigation_dist(const SearchArgs& a, const unsigned char* qs,
+                                                    int w, int lane) {
+  if (MODE == kModeBF16 || MODE == kModeFP8) return nav_dist_warp<MODE>(a, qs, w, lane);
+  return exact_dist_warp<MODE>(a, qs, w, lane);
+}
+
 template <int MODE, int NB>
 __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned char* ws,
                           const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int lane) {
@@ -298,7 +347,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
 
   // ---- query vector into shared memory
   if (job.query) {
-    const int qbytes = (MODE == kModeExactF32) ? d * 4 : d;
+    const int qbytes = mode_f32(MODE) ? d * 4 : d;
     const unsigned* src = static_cast<const unsigned*>(job.query);
     unsigned* dst = reinterpret_cast<unsigned*>(qs);
     for (int j = lane; j < (qbytes >> 2); j += 32) dst[j] = __ldg(src + j);
@@ -319,6 +368,24 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
     }
     __syncwarp();
   }
+  // float PQ: T[m][c] in FP32 (float codebook)
+  float* lutf = reinterpret_cast<float*>(ws + lay.lut);
+  if (MODE == kModePqF32) {
+    const float* qf = reinterpret_cast<const float*>(qs);
+    const int dsub = a.dsub;
+    for (int m = 0; m < a.M; ++m) {
+      for (int c = lane; c < 256; c += 32) {
+        const float* cc = a.cb_f32 + (static_cast<size_t>(m) * 256 + c) * dsub;
+        float acc = 0.f;
+        for (int j = 0; j < dsub; ++j) {
+          const float t = qf[m * dsub + j] - __ldg(cc + j);
+          acc = fmaf(t, t, acc);
+        }
+        lutf[m * 256 + c] = acc;
+      }
+    }
+    __syncwarp();
+  }
 
   // ---- a2: entry node
   unsigned entry_dist;
@@ -327,8 +394,14 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
     unsigned part = 0;
     for (int m = lane; m < a.M; m += 32) part += lut[m * 256 + code[m]];
     entry_dist = warp_sum_u32(part);
+  } else if (MODE == kModePqF32) {
+    // same summation order as the neighbours' lookups (m ascending)
+    float acc = 0.f;
+    const uint8_t* code = a.codes + static_cast<size_t>(a.entry) * a.M;
+    for (int m = 0; m < a.M; ++m) acc += lutf[m * 256 + code[m]];
+    entry_dist = __float_as_uint(acc);
   } else {
-    entry_dist = exact_dist_warp<MODE>(a, qs, a.entry, lane);
+    entry_dist = navigation_dist<MODE>(a, qs, a.entry, lane);
   }
   if (lane == 0) {
     s.keys[0] = make_key(entry_dist, a.entry);
@@ -389,7 +462,8 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       --inflight;
       ++steps;
 
-      // ---- a6: exact distance of u into the results
+      // ---- a6: exact distance of u into the results (the other modes keep
+      // their navigation distance here; a rerank pass follows where needed)
       unsigned long long rkey;
       if (MODE == kModePqU8) {
         const unsigned* xw = reinterpret_cast<const unsigned*>(blk);
@@ -422,7 +496,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       // PQ codes of every listed neighbour, issued before the visited probes
       // so that both round trips overlap.
       uint4 code[NB][kMaxM / 16];
-      if (MODE == kModePqU8) {
+      if (mode_pq(MODE)) {
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           if (w[t] >= 0) {
@@ -455,7 +529,30 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
 
       // ---- a8: navigation distances of the neighbours not known to be seen
       unsigned long long key[NB];
-      if (MODE == kModePqU8) {
+      if (MODE == kModePqF32) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          key[t] = kNoKey;
+          if (fresh[t] || pending[t]) {
+            float dist = 0.f;
+#pragma unroll
+            for (int c = 0; c < kMaxM / 16; ++c) {
+              if (c < (a.M >> 4)) {
+                const unsigned wd[4] = {code[t][c].x, code[t][c].y, code[t][c].z, code[t][c].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int m0 = c * 16 + e * 4;
+                  dist += lutf[(m0 + 0) * 256 + (wd[e] & 0xff)];
+                  dist += lutf[(m0 + 1) * 256 + ((wd[e] >> 8) & 0xff)];
+                  dist += lutf[(m0 + 2) * 256 + ((wd[e] >> 16) & 0xff)];
+                  dist += lutf[(m0 + 3) * 256 + (wd[e] >> 24)];
+                }
+              }
+            }
+            key[t] = make_key(__float_as_uint(dist), static_cast<unsigned>(w[t]));
+          }
+        }
+      } else if (MODE == kModePqU8) {
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
@@ -487,7 +584,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
             const int src_lane = __ffs(m) - 1;
             m &= m - 1;
             const int id = __shfl_sync(kFull, w[t], src_lane);
-            const unsigned dist = exact_dist_warp<MODE>(a, qs, id, lane);
+            const unsigned dist = navigation_dist<MODE>(a, qs, id, lane);
             if (lane == src_lane) key[t] = make_key(dist, static_cast<unsigned>(id));
           }
         }
@@ -595,7 +692,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
     const bool ok = r != kNoKey;
     job.ids[j] = ok ? static_cast<int32_t>(r & 0xffffffffu) : -1;
     const unsigned dbits = static_cast<unsigned>(r >> 32);
-    job.dists[j] = ok ? ((MODE == kModeExactF32) ? __uint_as_float(dbits) : static_cast<float>(dbits))
+    job.dists[j] = ok ? (mode_f32(MODE) ? __uint_as_float(dbits) : static_cast<float>(dbits))
                       : __int_as_float(0x7f800000);
   }
   // Clear the slots this query used, so the table is all zero for the next
@@ -633,7 +730,7 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
     qi = __shfl_sync(kFull, qi, 0);
     if (qi >= a.nq) break;
     QueryJob job;
-    const int qbytes = (MODE == kModeExactF32) ? a.d * 4 : a.d;
+    const int qbytes = mode_f32(MODE) ? a.d * 4 : a.d;
     job.query = static_cast<const uint8_t*>(a.queries) + static_cast<size_t>(qi) * qbytes;
     job.k = a.k;
     job.L = a.L;
@@ -797,18 +894,24 @@ using OccFn = cudaError_t (*)(int, int, int*);
 int nb_index(int nb) { return nb == 1 ? 0 : (nb == 2 ? 1 : 2); }
 
 LaunchFn launch_table(int mode, int nb) {
-  static const LaunchFn t[3][3] = {
+  static const LaunchFn t[kNumModes][3] = {
       {launch_t<kModePqU8, 1>, launch_t<kModePqU8, 2>, launch_t<kModePqU8, 4>},
       {launch_t<kModeExactU8, 1>, launch_t<kModeExactU8, 2>, launch_t<kModeExactU8, 4>},
-      {launch_t<kModeExactF32, 1>, launch_t<kModeExactF32, 2>, launch_t<kModeExactF32, 4>}};
+      {launch_t<kModeExactF32, 1>, launch_t<kModeExactF32, 2>, launch_t<kModeExactF32, 4>},
+      {launch_t<kModeBF16, 1>, launch_t<kModeBF16, 2>, launch_t<kModeBF16, 4>},
+      {launch_t<kModeFP8, 1>, launch_t<kModeFP8, 2>, launch_t<kModeFP8, 4>},
+      {launch_t<kModePqF32, 1>, launch_t<kModePqF32, 2>, launch_t<kModePqF32, 4>}};
   return t[mode][nb_index(nb)];
 }
 
 OccFn occ_table(int mode, int nb) {
-  static const OccFn t[3][3] = {
+  static const OccFn t[kNumModes][3] = {
       {occupancy_t<kModePqU8, 1>, occupancy_t<kModePqU8, 2>, occupancy_t<kModePqU8, 4>},
       {occupancy_t<kModeExactU8, 1>, occupancy_t<kModeExactU8, 2>, occupancy_t<kModeExactU8, 4>},
-      {occupancy_t<kModeExactF32, 1>, occupancy_t<kModeExactF32, 2>, occupancy_t<kModeExactF32, 4>}};
+      {occupancy_t<kModeExactF32, 1>, occupancy_t<kModeExactF32, 2>, occupancy_t<kModeExactF32, 4>},
+      {occupancy_t<kModeBF16, 1>, occupancy_t<kModeBF16, 2>, occupancy_t<kModeBF16, 4>},
+      {occupancy_t<kModeFP8, 1>, occupancy_t<kModeFP8, 2>, occupancy_t<kModeFP8, 4>},
+      {occupancy_t<kModePqF32, 1>, occupancy_t<kModePqF32, 2>, occupancy_t<kModePqF32, 4>}};
   return t[mode][nb_index(nb)];
 }
 
@@ -855,10 +958,13 @@ cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStrea
 cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,
                          cudaStream_t stream) {
   using ServeFn = cudaError_t (*)(const SearchArgs&, const ServeArgs&, const SearchPlan&, cudaStream_t);
-  static const ServeFn t[3][3] = {
+  static const ServeFn t[kNumModes][3] = {
       {launch_serve_t<kModePqU8, 1>, launch_serve_t<kModePqU8, 2>, launch_serve_t<kModePqU8, 4>},
       {launch_serve_t<kModeExactU8, 1>, launch_serve_t<kModeExactU8, 2>, launch_serve_t<kModeExactU8, 4>},
-      {launch_serve_t<kModeExactF32, 1>, launch_serve_t<kModeExactF32, 2>, launch_serve_t<kModeExactF32, 4>}};
+      {launch_serve_t<kModeExactF32, 1>, launch_serve_t<kModeExactF32, 2>, launch_serve_t<kModeExactF32, 4>},
+      {launch_serve_t<kModeBF16, 1>, launch_serve_t<kModeBF16, 2>, launch_serve_t<kModeBF16, 4>},
+      {launch_serve_t<kModeFP8, 1>, launch_serve_t<kModeFP8, 2>, launch_serve_t<kModeFP8, 4>},
+      {launch_serve_t<kModePqF32, 1>, launch_serve_t<kModePqF32, 2>, launch_serve_t<kModePqF32, 4>}};
   return t[plan.mode][nb_index(plan.nb)](a, s, plan, stream);
 }
 

@@ -74,6 +74,8 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   int mode = 0, slot_bytes = 0;
   int rc = index_search_view(ix, &a, &mode, &slot_bytes);
   if (rc != ANN_OK) return rc;
+  if (mode == kModeBF16 || mode == kModeFP8 || mode == kModePqF32)
+    return set_error(ANN_EINVAL, "compressed-navigation indexes need the rerank pass: use ann_search_dev");
   void* base = nullptr;
   rc = scratch_address(&base);  // first call on a device: symbol lookup
   if (rc != ANN_OK) return rc;

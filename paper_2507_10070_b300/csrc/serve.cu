@@ -154,6 +154,10 @@ int ann_serve_create(ann_index* ix, const ann_serve_cfg* cfg, ann_server** out) 
     delete s;
     return rc;
   }
+  if (s->mode == kModeBF16 || s->mode == kModeFP8 || s->mode == kModePqF32) {
+    delete s;
+    return set_error(ANN_EINVAL, "compressed-navigation indexes need the rerank pass: serve a PQ-u8 or exact index");
+  }
   cudaError_t e = cudaGetDevice(&s->device);
   if (e != cudaSuccess) {
     delete s;

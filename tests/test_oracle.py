@@ -273,3 +273,30 @@ def test_inmemory_workload_recall():
     assert r0 >= 0.95 and abs(r1 - r0) <= 0.01
     assert 1.0 <= s1.mean() / s0.mean() <= 1.10
     assert _bfs_reach(adj, med) >= 9990
+
+
+def test_navigation_vectors_and_rerank_hand_worked():
+    """Navigation on separate vectors, then an exact rerank of the best by
+    navigation (the precision workload's FP32 rerank of the top candidates).
+    1-d points, query 0, star graph from node 0 (L=5: all expanded).
+      exact d^2:      x = [100, 10, 8, 6, 4]  -> [10000, 100, 64, 36, 16]
+      navigation d^2: v = [100, 1, 2, 3, 50]  -> [10000, 1, 4, 9, 2500]
+    Best 3 by navigation: nodes 1, 2, 3; their exact ranking: 3 (36), 2 (64),
+    1 (100).  Without a rerank every expanded node is ranked exactly: 4 (16)."""
+    base = np.array([[100], [10], [8], [6], [4]], np.float32)
+    nav = np.array([[100], [1], [2], [3], [50]], np.float64)
+    adj = np.array([[1, 2, 3, 4]] + [[-1, -1, -1, -1]] * 4, np.int32)
+    q = np.zeros((1, 1), np.float32)
+    ids, d, _ = oracle.search(base, adj, 0, q, 2, 5, 0, nav_vectors=nav, rerank=3)
+    assert ids[0].tolist() == [3, 2] and d[0].tolist() == [36.0, 64.0]
+    ids, d, _ = oracle.search(base, adj, 0, q, 2, 5, 0, nav_vectors=nav)
+    assert ids[0].tolist() == [4, 3] and d[0].tolist() == [16.0, 36.0]
+    # navigation on the base itself with a full rerank equals the plain search
+    mx = datagen.inmemory_f32()
+    b, qq = mx.base(2000), mx.queries(20)
+    med = oracle.medoid(b)
+    g = oracle.vamana(b, 16, 1.2, 32, med, datagen.build_order(mx.seed, 2000),
+                      datagen.random_out_neighbours(mx.seed, 2000, 16))
+    a = oracle.search(b, g, med, qq, 10, 32, 1)
+    r = oracle.search(b, g, med, qq, 10, 32, 1, nav_vectors=b.astype(np.float64), rerank=32)
+    assert np.array_equal(a[0], r[0]) and np.array_equal(a[1], r[1])
