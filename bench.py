@@ -401,6 +401,78 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
             "seconds": round(wall, 2)}
 
 
+def run_precision(args):
+    """Precision workload: DEEP-like float32 vectors (d=96, unit-normalised,
+    mixture of 1,024 Gaussians, sigma 0.05 before normalising), Vamana R=48
+    (built on the GPU, off the clock), 10,000 queries, k=10.  Navigation on
+    FP32 (the reference traversal), BF16, FP8-E4M3 (x * 64) and 48-byte float
+    PQ (48 subspaces x 2 dims) vectors, FP32 accumulation; the compressed
+    variants rerank their top 4k expanded candidates exactly in FP32.  For
+    each: recall@10 (exact GPU ground truth), QPS (queries resident in HBM,
+    CUDA-event timed), and the largest relative error of the returned
+    distances against float64."""
+    import torch
+    import paper_2507_10070_b300 as ann
+    torch.cuda.set_device(0)
+    n, nq, k = args.precision_n, 10_000, 10
+    mx = datagen.deep_like()
+    t0 = time.time()
+    base, q = mx.base(n), mx.queries(nq)
+    os.makedirs(DATA, exist_ok=True)
+    path = os.path.join(DATA, f"deep_like_n{n}_R48_M48.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        adj, entry, cb, codes, gi, gd = z["adj"], int(z["entry"]), z["cb"], z["codes"], z["gi"], z["gd"]
+    else:
+        adj, entry = ann.build_graph(base, 48, 1.2, 96, seed=mx.seed, device="gpu")
+        cb, codes = ann.build_pq(base, 48, n_train=100_000, iters=25,
+                                 kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, 48))
+        gi, gd = ann.knn_exact(base, q, k)
+        np.savez(path, adj=adj, entry=entry, cb=cb, codes=codes, gi=gi, gd=gd)
+    setup = time.time() - t0
+    qd = torch.from_numpy(q).cuda()
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    variants = {
+        "fp32": dict(),
+        "bf16": dict(nav=ann.ANN_NAV_BF16),
+        "fp8_e4m3": dict(nav=ann.ANN_NAV_FP8, nav_scale=64.0),
+        "pq48": dict(codebook=cb, codes=codes),
+    }
+    out = {"what": run_precision.__doc__.split("\n\n")[0].replace("\n", " "), "n": n, "nq": nq,
+           "k": k, "depth": 1, "setup_s": round(setup, 1), "variants": {}}
+    for name, kw in variants.items():
+        if "codebook" in kw:
+            ix = ann.Index(base, adj, entry, kw["codebook"], kw["codes"], tier=ann.ANN_TIER_HBM)
+        else:
+            ix = ann.Index(base, adj, entry, tier=ann.ANN_TIER_HBM, nav=kw.get("nav", 0),
+                           nav_scale=kw.get("nav_scale", 0.0))
+        rows = []
+        for L in args.precision_Ls:
+            ix.search_dev(qd, k, L, 1, ids, dists, stream=st)
+            ix.sync(st)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(st)
+            for _ in range(3):
+                ix.search_dev(qd, k, L, 1, ids, dists, stream=st)
+            ev[1].record(st)
+            ix.sync(st)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / 3
+            hi, hd = ids.cpu().numpy(), dists.cpu().numpy()
+            r = ann.recall_at_k(hi, gi, gd, hd)
+            x = base[np.maximum(hi, 0)].astype(np.float64)
+            d64 = ((x - q[:, None, :].astype(np.float64)) ** 2).sum(-1)
+            ok = hi >= 0
+            err = float(np.max(np.abs(hd[ok] - d64[ok]) / np.maximum(d64[ok], 1e-30)))
+            rows.append({"L": L, "recall_at_10": round(r, 4), "qps": round(nq / (ms * 1e-3), 1),
+                         "max_rel_dist_error_vs_fp64": float(f"{err:.3g}")})
+        ix.close()
+        out["variants"][name] = rows
+    return out
+
+
 def cpu_baseline(w, L: int, sample: int):
     """The CPU oracle as it stands (synchronous search, every host core) on the
     first `sample` queries of the same workload and index."""
@@ -476,11 +548,18 @@ def main():
     ap.add_argument("--autotune", type=int, default=1, help="run the degree selector (1) or not (0)")
     ap.add_argument("--builder", choices=["cpu", "gpu"], default="gpu",
                     help="Vamana construction for the index (off the clock)")
+    ap.add_argument("--precision", action="store_true",
+                    help="only run the precision workload (float32 DEEP-like, BF16/FP8/PQ navigation)")
+    ap.add_argument("--precision-n", type=int, default=10_000_000)
+    ap.add_argument("--precision-Ls", type=int, nargs="+", default=[32, 64, 128, 256, 512])
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only print the storage-tier probe's GB/s for several read sizes")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.precision:
+        print(json.dumps(run_precision(args)), flush=True)
+        return
     if args.probe_sweep:
         import paper_2507_10070_b300 as ann
         out = {"probe": "random reads of a 1 GiB region, full-occupancy grid, 4 reads in flight per warp"}

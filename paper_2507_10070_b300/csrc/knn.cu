@@ -4,9 +4,10 @@
 //  1. dist_tile: a 64-query x 64-row tile per block, 256 threads each owning
 //     a 4x4 sub-tile; query and base rows staged in shared memory.  uint8
 //     distances are exact integers (__vabsdiffu4 + __dp4a); float32 uses FP32.
-//  2. topk_rows: one block per query scans its row of the distance matrix;
-//     each thread keeps an ascending top-k of (distance, id) keys, then k
-//     rounds of a block-wide minimum pop the global top-k.
+//  2. topk_segments + topk_merge: each row of the distance matrix is split
+//     into 2^17-entry segments, one block per segment keeps the segment's
+//     top-k (per-thread ascending lists, then k rounds of a block-wide
+//     minimum), and one block per query merges the segments' candidates.
 // Keys are (distance bits << 32 | id): the order is (distance, id) because
 // non-negative float bit patterns sort like the floats they encode.
 #include <cstdint>
@@ -71,29 +72,29 @@ __global__ void __launch_bounds__(256) dist_tile(const void* __restrict__ base, 
     }
 }
 
-__global__ void __launch_bounds__(256) topk_rows(const unsigned* __restrict__ dist, int64_t n,
-                                                 int k, int32_t* __restrict__ ids,
-                                                 float* __restrict__ dists, bool u8) {
+// Per-block selection of the k smallest keys among `cnt` keys produced by
+// get(i): every thread keeps an ascending top-k of its strided share, then k
+// rounds of a block-wide minimum pop the block's top-k (written to out[0..k)).
+template <class Get>
+__device__ void block_topk(Get get, int64_t cnt, int k, unsigned long long* out) {
   __shared__ unsigned long long red[256];
   unsigned long long top[kMaxK];
   const int tid = threadIdx.x;
-  const unsigned* row = dist + static_cast<int64_t>(blockIdx.x) * n;
-  int cnt = 0;
-  for (int64_t i = tid; i < n; i += blockDim.x) {
-    const unsigned long long key = (static_cast<unsigned long long>(row[i]) << 32) |
-                                   static_cast<unsigned>(i);
-    if (cnt == k && key >= top[k - 1]) continue;
-    int p = cnt < k ? cnt : k - 1;
+  int have = 0;
+  for (int64_t i = tid; i < cnt; i += blockDim.x) {
+    const unsigned long long key = get(i);
+    if (key == ~0ull || (have == k && key >= top[k - 1])) continue;
+    int p = have < k ? have : k - 1;
     while (p > 0 && top[p - 1] > key) {
       top[p] = top[p - 1];
       --p;
     }
     top[p] = key;
-    if (cnt < k) ++cnt;
+    if (have < k) ++have;
   }
   int head = 0;
   for (int r = 0; r < k; ++r) {
-    red[tid] = head < cnt ? top[head] : ~0ull;
+    red[tid] = head < have ? top[head] : ~0ull;
     __syncthreads();
     for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
       if (tid < s && red[tid + s] < red[tid]) red[tid] = red[tid + s];
@@ -101,14 +102,39 @@ __global__ void __launch_bounds__(256) topk_rows(const unsigned* __restrict__ di
     }
     const unsigned long long best = red[0];
     __syncthreads();
-    if (head < cnt && top[head] == best) ++head;
-    if (tid == 0) {
-      const bool ok = best != ~0ull;
-      const unsigned db = static_cast<unsigned>(best >> 32);
-      ids[static_cast<int64_t>(blockIdx.x) * k + r] = ok ? static_cast<int32_t>(best & 0xffffffffu) : -1;
-      dists[static_cast<int64_t>(blockIdx.x) * k + r] =
-          ok ? (u8 ? static_cast<float>(db) : __uint_as_float(db)) : __int_as_float(0x7f800000);
-    }
+    if (head < have && top[head] == best) ++head;
+    if (tid == 0) out[r] = best;
+  }
+}
+
+// Stage 1: block (q, s) selects the top-k of segment s of distance row q.
+__global__ void __launch_bounds__(256) topk_segments(const unsigned* __restrict__ dist, int64_t n,
+                                                     int64_t seg, int k,
+                                                     unsigned long long* __restrict__ part) {
+  const int64_t q = blockIdx.x, s = blockIdx.y;
+  const int64_t lo = s * seg, hi = lo + seg < n ? lo + seg : n;
+  const unsigned* row = dist + q * n;
+  block_topk([&](int64_t i) {
+    const int64_t c = lo + i;
+    return (static_cast<unsigned long long>(row[c]) << 32) | static_cast<unsigned>(c);
+  }, hi > lo ? hi - lo : 0, k, part + (q * gridDim.y + s) * k);
+}
+
+// Stage 2: block q merges its segments' candidates into the final top-k.
+__global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __restrict__ part, int nseg,
+                                                  int k, int32_t* __restrict__ ids,
+                                                  float* __restrict__ dists, bool u8) {
+  __shared__ unsigned long long best[kMaxK];
+  const int64_t q = blockIdx.x;
+  const unsigned long long* p = part + q * nseg * k;
+  block_topk([&](int64_t i) { return p[i]; }, (int64_t)nseg * k, k, best);
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    const unsigned long long b = best[r];
+    const bool ok = b != ~0ull;
+    const unsigned db = static_cast<unsigned>(b >> 32);
+    ids[q * k + r] = ok ? static_cast<int32_t>(b & 0xffffffffu) : -1;
+    dists[q * k + r] = ok ? (u8 ? static_cast<float>(db) : __uint_as_float(db)) : __int_as_float(0x7f800000);
   }
 }
 
@@ -125,9 +151,18 @@ cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, cons
   chunk = chunk / kTile * kTile;
   if (chunk < kTile) chunk = kTile;
   if (chunk > nq) chunk = (nq + kTile - 1) / kTile * kTile;
+  // each distance row is scanned by nseg blocks of `seg` entries, then merged
+  const int64_t seg = 1 << 17;
+  const int nseg = static_cast<int>((n + seg - 1) / seg);
   unsigned* dmat = nullptr;
+  unsigned long long* part = nullptr;
   cudaError_t e = cudaMalloc(&dmat, static_cast<size_t>(chunk) * n * sizeof(unsigned));
   if (e != cudaSuccess) return e;
+  e = cudaMalloc(&part, static_cast<size_t>(chunk) * nseg * k * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaFree(dmat);
+    return e;
+  }
   if (u8) e = cudaFuncSetAttribute(dist_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else e = cudaFuncSetAttribute(dist_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int64_t q0 = 0; q0 < nq && e == cudaSuccess; q0 += chunk) {
@@ -138,12 +173,13 @@ cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, cons
     const void* qp = static_cast<const uint8_t*>(queries) + q0 * d * elt;
     if (u8) dist_tile<true><<<grid, 256, smem, stream>>>(base, n, d, qp, m, dmat);
     else dist_tile<false><<<grid, 256, smem, stream>>>(base, n, d, qp, m, dmat);
-    topk_rows<<<static_cast<unsigned>(m), 256, 0, stream>>>(dmat, n, k, ids + q0 * k,
-                                                            dists + q0 * k, u8);
+    topk_segments<<<dim3(static_cast<unsigned>(m), nseg), 256, 0, stream>>>(dmat, n, seg, k, part);
+    topk_merge<<<static_cast<unsigned>(m), 256, 0, stream>>>(part, nseg, k, ids + q0 * k, dists + q0 * k, u8);
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaStreamSynchronize(stream);
   cudaFree(dmat);
+  cudaFree(part);
   return e != cudaSuccess ? e : e2;
 }
 
