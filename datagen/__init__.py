@@ -16,11 +16,17 @@ chunk size used to generate it.
 
 Streams: 0 centres, 1 base vectors, 2 queries, 3 PQ training randomness,
 4 graph-build randomness.  Workload seeds are 2507_10070 + workload number.
+
+Because the generator is counter-based, any run of vectors can be drawn on
+its own (the stream jumps to draw i*(d+1)); large bases are generated in
+parallel worker processes into shared memory, with the same result as a
+sequential pass.
 """
 from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -37,9 +43,14 @@ _CHUNK = 1 << 16
 class Stream:
     """Sequential uniform/normal source on one (seed, stream) Philox key."""
 
-    def __init__(self, seed: int, stream: int):
+    def __init__(self, seed: int, stream: int, position: int = 0):
         key = np.array([seed & 0xFFFFFFFFFFFFFFFF, stream], dtype=np.uint64)
         self._bg = np.random.Philox(key=key)
+        if position:
+            # Philox produces 4 outputs per counter step
+            self._bg.advance(position // 4)
+            if position % 4:
+                self._bg.random_raw(position % 4)
 
     def raw(self, count: int) -> np.ndarray:
         return self._bg.random_raw(int(count)).astype(np.uint64)
@@ -78,32 +89,75 @@ class Mixture:
         s = Stream(self.seed, STREAM_CENTRES)
         return self.lo + (self.hi - self.lo) * s.uniform((self.n_centres, self.d))
 
-    def _draw(self, stream: int, n: int, start_chunk_cb=None) -> np.ndarray:
+    def _draw_rows(self, stream: int, lo: int, hi: int, out: np.ndarray) -> None:
+        """Rows [lo, hi) of the stream into out[0:hi-lo]."""
         assert self.d % 2 == 0, "Box-Muller pairs need an even dimension"
         c = self.centres()
-        s = Stream(self.seed, stream)
-        dtype = np.uint8 if self.kind == "u8" else np.float32
-        out = np.empty((n, self.d), dtype=dtype)
-        for lo in range(0, n, _CHUNK):
-            m = min(_CHUNK, n - lo)
+        s = Stream(self.seed, stream, position=lo * (self.d + 1))
+        for a in range(lo, hi, _CHUNK):
+            m = min(_CHUNK, hi - a)
             u = s.uniform((m, self.d + 1))
             comp = np.minimum((u[:, 0] * self.n_centres).astype(np.int64),
                               self.n_centres - 1)
             x = c[comp] + self.sigma * _box_muller(u[:, 1:])
+            dst = out[a - lo:a - lo + m]
             if self.kind == "u8":
-                out[lo:lo + m] = np.clip(np.rint(x), 0, 255).astype(np.uint8)
+                dst[:] = np.clip(np.rint(x), 0, 255).astype(np.uint8)
             elif self.kind == "f32_unit":
                 x /= np.linalg.norm(x, axis=1, keepdims=True)
-                out[lo:lo + m] = x.astype(np.float32)
+                dst[:] = x.astype(np.float32)
             else:
-                out[lo:lo + m] = x.astype(np.float32)
+                dst[:] = x.astype(np.float32)
+
+    def _draw(self, stream: int, n: int, workers: int | None = None) -> np.ndarray:
+        assert self.d % 2 == 0, "Box-Muller pairs need an even dimension"
+        dtype = np.uint8 if self.kind == "u8" else np.float32
+        workers = workers if workers is not None else (os.cpu_count() or 1)
+        if n >= 4 * _PAR_ROWS and workers > 1:
+            return _draw_parallel(self, stream, n, dtype, workers)
+        out = np.empty((n, self.d), dtype=dtype)
+        self._draw_rows(stream, 0, n, out)
         return out
 
-    def base(self, n: int) -> np.ndarray:
-        return self._draw(STREAM_BASE, n)
+    def base(self, n: int, workers: int | None = None) -> np.ndarray:
+        return self._draw(STREAM_BASE, n, workers)
 
     def queries(self, nq: int) -> np.ndarray:
-        return self._draw(STREAM_QUERIES, nq)
+        return self._draw(STREAM_QUERIES, nq, 1)
+
+
+_PAR_ROWS = 1 << 20  # rows per worker task
+
+
+def _fill_task(args):
+    from multiprocessing import shared_memory
+    mixture, stream, lo, hi, name, n, dtype = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        arr = np.ndarray((n, mixture.d), dtype=dtype, buffer=shm.buf)
+        mixture._draw_rows(stream, lo, hi, arr[lo:hi])
+    finally:
+        shm.close()
+    return hi - lo
+
+
+def _draw_parallel(mixture, stream, n, dtype, workers):
+    """Rows drawn by worker processes (spawned, so safe after CUDA is up)
+    into shared memory; identical to the sequential draw."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    nbytes = n * mixture.d * np.dtype(dtype).itemsize
+    shm = shared_memory.SharedMemory(create=True, size=max(nbytes, 1))
+    try:
+        tasks = [(mixture, stream, lo, min(n, lo + _PAR_ROWS), shm.name, n, dtype)
+                 for lo in range(0, n, _PAR_ROWS)]
+        with mp.get_context("spawn").Pool(min(workers, len(tasks))) as pool:
+            assert sum(pool.map(_fill_task, tasks)) == n
+        out = np.ndarray((n, mixture.d), dtype=dtype, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return out
 
 
 def inmemory_f32(seed_offset: int = 1, d: int = 128, n_centres: int = 32) -> Mixture:

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ann_internal.h"
@@ -97,6 +98,20 @@ namespace {
 
 int elt_size(int dtype) { return dtype == ANN_U8 ? 1 : 4; }
 
+// Static split of [0, n) over the host's hardware threads.
+template <class F>
+void host_parallel(int64_t n, F&& fn) {
+  const int th = static_cast<int>(std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()),
+                                                    std::max<int64_t>(1, n / 65536)));
+  if (th <= 1) {
+    fn(0, n);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < th; ++t) pool.emplace_back([&, t] { fn(n * t / th, n * (t + 1) / th); });
+  for (auto& x : pool) x.join();
+}
+
 void release(ann_index* ix) {
   if (!ix) return;
   if (ix->blocks_host) cudaFreeHost(ix->blocks_host);
@@ -157,10 +172,20 @@ int validate_desc(const ann_graph_desc* g) {
   } else if (g->tier != ANN_TIER_HBM) {
     return set_error(ANN_EINVAL, "exact navigation keeps vectors in HBM: use ANN_TIER_HBM");
   }
-  for (int64_t i = 0; i < g->n * g->R; ++i) {
-    const int32_t v = g->adj[i];
-    if (v < -1 || v >= g->n) return set_error(ANN_EINVAL, "adjacency id %d at row %lld out of range", v, (long long)(i / g->R));
-  }
+  std::atomic<int64_t> bad{-1};
+  host_parallel(g->n * g->R, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      const int32_t v = g->adj[i];
+      if (v < -1 || v >= g->n) {
+        int64_t expect = -1;
+        bad.compare_exchange_strong(expect, i);
+        return;
+      }
+    }
+  });
+  if (bad.load() >= 0)
+    return set_error(ANN_EINVAL, "adjacency id %d at row %lld out of range", g->adj[bad.load()],
+                     (long long)(bad.load() / g->R));
   return ANN_OK;
 }
 
@@ -235,20 +260,22 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
       dst = tmp.data();
     }
     const uint8_t* vec = static_cast<const uint8_t*>(g->vectors);
-    for (int64_t i = 0; i < n; ++i) {
-      uint8_t* b = dst + (size_t)i * ix->block_bytes;
-      std::memset(b, 0, ix->block_bytes);
-      std::memcpy(b, vec + (size_t)i * d, d);
-      int32_t* ids = reinterpret_cast<int32_t*>(b + ix->ids_off);
-      uint32_t deg = 0;
-      for (int j = 0; j < R; ++j) {
-        const int32_t v = g->adj[(size_t)i * R + j];
-        if (v < 0) break;
-        ids[deg++] = v;
+    host_parallel(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        uint8_t* b = dst + (size_t)i * ix->block_bytes;
+        std::memset(b, 0, ix->block_bytes);
+        std::memcpy(b, vec + (size_t)i * d, d);
+        int32_t* ids = reinterpret_cast<int32_t*>(b + ix->ids_off);
+        uint32_t deg = 0;
+        for (int j = 0; j < R; ++j) {
+          const int32_t v = g->adj[(size_t)i * R + j];
+          if (v < 0) break;
+          ids[deg++] = v;
+        }
+        for (int j = deg; j < R; ++j) ids[j] = -1;
+        std::memcpy(b + ix->deg_off, &deg, 4);
       }
-      for (int j = deg; j < R; ++j) ids[j] = -1;
-      std::memcpy(b + ix->deg_off, &deg, 4);
-    }
+    });
     if (g->tier == ANN_TIER_HOST_PINNED) {
       ANN_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ix->blocks_dev), ix->blocks_host, 0),
               "cudaHostGetDevicePointer");
@@ -281,12 +308,14 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
     ix->block_bytes = ix->adj_stride * 4;
     ix->slot_bytes = ix->block_bytes;
     std::vector<int32_t> rows((size_t)n * ix->adj_stride, -1);
-    for (int64_t i = 0; i < n; ++i)
-      for (int j = 0; j < R; ++j) {
-        const int32_t v = g->adj[(size_t)i * R + j];
-        if (v < 0) break;
-        rows[(size_t)i * ix->adj_stride + j] = v;
-      }
+    host_parallel(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i)
+        for (int j = 0; j < R; ++j) {
+          const int32_t v = g->adj[(size_t)i * R + j];
+          if (v < 0) break;
+          rows[(size_t)i * ix->adj_stride + j] = v;
+        }
+    });
     ANN_TRY(cudaMalloc(&ix->adj, rows.size() * 4), "cudaMalloc adjacency");
     ANN_TRY(cudaMemcpy(ix->adj, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice), "upload adjacency");
     const float* fv = static_cast<const float*>(g->vectors);

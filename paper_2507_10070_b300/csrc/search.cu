@@ -185,8 +185,8 @@ __device__ __forceinline__ void result_insert(unsigned long long* res, int& nres
 // Merge the sorted new candidates cand[0..c) into the list in place and keep
 // L entries.  rank_j = number of list entries below cand[j]; list entry i moves
 // to i + #{j : rank_j <= i} and cand[j] to j + rank_j.  Entries only move
-// right, so sweeping the tail in 32-entry chunks from the top down never
-// overwrites an entry not yet read; the candidates then fill the holes.
+// right, so sweeping the tail in blocks from the top down never overwrites
+// an entry not yet read; the candidates then fill the holes.
 // Entries before rank_0 keep their place.  Returns rank_0 (the first position
 // whose entry changed), or L if nothing entered.
 __device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned long long* cand,
@@ -196,30 +196,41 @@ __device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned lo
   for (int j = lane; j < c; j += 32) s.rank[j] = lower_bound_u64(s.keys, s.len, cand[j]);
   __syncwarp();
   const int pos0 = s.rank[0];
-  // p = #{j : rank_j <= top of the current chunk}
+  // Sweep the tail top-down in 128-entry blocks (four entries per lane, all
+  // read before any write).  p = #{j : rank_j <= top of the current block}.
+  constexpr int kB = 128;
   int p = c;
-  const int top_chunk = ((s.len - 1) >> 5) << 5;
-  while (p > 0 && s.rank[p - 1] > top_chunk + 31) --p;
-  for (int b = top_chunk; b >= (pos0 & ~31); b -= 32) {
-    const int i = b + lane;
-    const bool live = i >= pos0 && i < s.len;
-    unsigned long long key = 0;
-    unsigned char flag = 0;
-    if (live) {
-      key = s.keys[i];
-      flag = s.flags[i];
+  const int top_block = ((s.len - 1) / kB) * kB;
+  while (p > 0 && s.rank[p - 1] > top_block + kB - 1) --p;
+  for (int b = top_block; b >= (pos0 / kB) * kB; b -= kB) {
+    unsigned long long key[4];
+    unsigned char flag[4];
+    int r[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = b + t * 32 + lane;
+      const bool live = i >= pos0 && i < s.len;
+      key[t] = live ? s.keys[i] : 0ull;
+      flag[t] = live ? s.flags[i] : 0;
+      r[t] = p;
     }
-    // r(i) = p - #{j : i < rank_j <= b + 31}; walk the ranks inside this chunk
-    int r = p;
+    // r(i) = p - #{j : i < rank_j <= b + kB - 1}: walk the ranks inside this block
     while (p > 0 && s.rank[p - 1] >= b) {
       --p;
-      if (i < s.rank[p]) --r;
+      const int rk = s.rank[p];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (b + t * 32 + lane < rk) --r[t];
     }
     __syncwarp();
-    const int np = i + r;
-    if (live && np < L) {
-      s.keys[np] = key;
-      s.flags[np] = flag;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = b + t * 32 + lane;
+      const int np = i + r[t];
+      if (i >= pos0 && i < s.len && np < L) {
+        s.keys[np] = key[t];
+        s.flags[np] = flag[t];
+      }
     }
     __syncwarp();
   }

@@ -48,3 +48,15 @@ def test_build_randomness():
     for i in range(300):
         assert i not in g[i] and len(set(g[i].tolist())) == 16
     assert np.array_equal(g, datagen.random_out_neighbours(5, 300, 16))
+
+
+def test_parallel_generation_equals_sequential():
+    mx = datagen.sift_like()
+    n = 4 * datagen._PAR_ROWS + 12345          # several worker tasks and a ragged tail
+    par = mx.base(n, workers=4)
+    # spot-check rows against independent sequential draws of their runs
+    for lo in (0, datagen._PAR_ROWS - 3, 2 * datagen._PAR_ROWS + 7, n - 5):
+        chunk = np.empty((5, mx.d), np.uint8)
+        mx._draw_rows(datagen.STREAM_BASE, lo, lo + 5, chunk)
+        assert np.array_equal(par[lo:lo + 5], chunk)
+    assert np.array_equal(par[:70_000], mx.base(70_000, workers=1))
