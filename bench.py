@@ -38,6 +38,11 @@ sys.path.insert(0, ROOT)
 import datagen  # noqa: E402
 
 DATA = os.path.join(ROOT, "_data")
+# ncu counters of the current search kernel on a 200k-node case, per
+# expansion (profiles/search_kernel_pq_sift200k_L256.md): PCIe read bytes
+# (the storage tier, which bounds the kernel) and DRAM read + write bytes.
+NCU_PCIE_BYTES_PER_EXPANSION = 420.0
+NCU_DRAM_BYTES_PER_EXPANSION = 508.0
 METRIC = "QPS at recall@10>=0.95 on 1 B300, relaxed vs sync search; p50/p99 latency"
 WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Vamana R=64, PQ M=32 in HBM, 512 B node blocks in host pinned memory, k=10"
 
@@ -296,7 +301,10 @@ def run_ours(args, rank: int, world: int):
                 "h2d_bytes_per_step": int(w["q"].nbytes), "d2h_bytes_per_step": int(nq * k * 8)},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "pcie", "achieved": round(achieved, 2), "peak": round(probe_gbps, 2),
-                     "unit": "GB/s", "frac": round(achieved / probe_gbps, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / probe_gbps, 4),
+                     "traffic": int(NCU_PCIE_BYTES_PER_EXPANSION * st.expansions / args.steps),
+                     "traffic_what": "pcie__read_bytes.sum per launch (the bound's resource): ncu's bytes per expansion on the same kernel x this launch's expansions",
+                     "dram_traffic": int(NCU_DRAM_BYTES_PER_EXPANSION * st.expansions / args.steps),
                      "peak_source": f"measured in-run: random {fetch_bytes} B reads of host pinned memory (the search's per-expansion fetch) by a full-occupancy probe kernel (ann_probe_read_bandwidth)",
                      "algorithmic_bytes_per_launch": int(bytes_per_launch),
                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs")},
@@ -484,6 +492,108 @@ def run_precision(args):
     return out
 
 
+def run_large(args):
+    """Large out-of-core workload: SIFT-like uint8 vectors (d=128, mixture of
+    4,096 Gaussians, otherwise as the 1M workload), 10^8 of them by default;
+    Vamana R=64 built by the library's GPU tooling off the clock; 32-byte PQ
+    codes in HBM (3.2 GB at 10^8); 512-byte node blocks in host pinned memory
+    (51.2 GB at 10^8); 10,000 queries, k=10, L=128.  Each depth of the
+    pipeline is timed on the batched search (queries resident in HBM, L2
+    flushed between steps); the relaxed pipeline is reported at the fastest
+    depth > 0, next to the synchronous search (depth 0), and the serving loop
+    runs on the same index.  Recall@10 is against exact GPU ground truth; the
+    returned distances of a sample are checked against exact integer L2."""
+    import torch
+    import paper_2507_10070_b300 as ann
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, nq, k, L, R, M = args.large_n, 10_000, 10, args.large_L, 64, 32
+    mx = datagen.sift_like_large()
+    t_all = time.time()
+    prep = {}
+    t = time.time()
+    base, q = mx.base(n), mx.queries(nq)
+    prep["data_s"] = round(time.time() - t, 1)
+    t = time.time()
+    cb, codes = ann.build_pq(base, M, n_train=100_000, iters=25,
+                             kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, M), encode_device="gpu")
+    prep["pq_s"] = round(time.time() - t, 1)
+    t = time.time()
+    adj, entry = ann.build_graph(base, R, 1.2, args.large_Lb, seed=mx.seed, device="gpu")
+    prep["graph_gpu_s"] = round(time.time() - t, 1)
+    t = time.time()
+    gt_ids, gt_d = ann.knn_exact(base, q, k)
+    prep["ground_truth_s"] = round(time.time() - t, 1)
+    probe_1g = ann.probe_read_bandwidth(1 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
+    probe_16g = ann.probe_read_bandwidth(16 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
+    t = time.time()
+    ix = ann.Index(base, adj, entry, cb, codes, tier=ann.ANN_TIER_HOST_PINNED)
+    prep["index_load_s"] = round(time.time() - t, 1)
+    qd = torch.from_numpy(q).to(dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+
+    def timed(depth, K, W):
+        for _ in range(W):
+            ix.search_dev(qd, k, L, depth, ids, dists, stream=stream)
+        ix.sync(stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        for i in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            ix.search_dev(qd, k, L, depth, ids, dists, stream=stream)
+            ev[i][1].record(stream)
+        st = ix.sync(stream)
+        torch.cuda.synchronize()
+        return float(np.sum([a.elapsed_time(b) for a, b in ev])), st
+
+    by_depth = {}
+    with ClockSampler(0) as clk:
+        for depth in (0, 1, 2, 4):
+            ms, st = timed(depth, args.steps, args.warmup)
+            hi, hd = ids.cpu().numpy(), dists.cpu().numpy()
+            by_depth[depth] = {
+                "qps": round(nq * args.steps / (ms * 1e-3), 1),
+                "ms_per_step": round(ms / args.steps, 3),
+                "recall_at_10": round(ann.recall_at_k(hi, gt_ids, gt_d, hd), 4),
+                "mean_steps": round(st.expansions / max(st.queries, 1), 2),
+                "pcie_gbs": round(st.expansions * st.bytes_per_expansion / (ms * 1e-3) / 1e9, 2)}
+    best = max((1, 2, 4), key=lambda d: by_depth[d]["qps"])
+    ix.search_dev(qd, k, L, best, ids, dists, stream=stream)
+    ix.sync(stream)
+    hi, hd = ids.cpu().numpy(), dists.cpu().numpy()
+    s = np.arange(0, nq, 10)
+    x = base[hi[s]].astype(np.int64)
+    exact = ((x - q[s][:, None, :].astype(np.int64)) ** 2).sum(-1)
+    checks = {"sampled_queries": int(s.size),
+              "distances_equal_exact_l2": bool(np.array_equal(hd[s].astype(np.int64), exact)),
+              "ids_distinct": bool(all(len(set(r.tolist())) == k for r in hi)),
+              "distances_sorted": bool(np.all(np.diff(hd, axis=1) >= 0))}
+    out = {"what": run_large.__doc__.split("\n\n")[0].replace("\n", " "),
+           "n": n, "nq": nq, "k": k, "L": L, "R": R, "M": M, "L_build": args.large_Lb,
+           "host_pinned_node_blocks_gb": round(n * ix.block_bytes / 1e9, 1),
+           "hbm_pq_codes_gb": round(n * M / 1e9, 2),
+           "value": by_depth[best]["qps"], "unit": "queries/s", "depth": best,
+           "recall_at_10": by_depth[best]["recall_at_10"],
+           "sync": by_depth[0], "relaxed_over_sync": round(by_depth[best]["qps"] / by_depth[0]["qps"], 4),
+           "by_depth": {str(d): v for d, v in by_depth.items()},
+           "probe_gbs_384B": {"1GiB_region": round(probe_1g, 2), "16GiB_region": round(probe_16g, 2)},
+           "checks": checks, "prep": prep, "clocks": clk.summary()}
+    if args.serve_seconds > 0:
+        out["serving"] = run_serving(ix, {"q": q}, gt_ids, gt_d, L, best, args.serve_seconds)
+    if not args.no_cpu_baseline:
+        w = {"base": base, "adj": adj, "entry": entry, "cb": cb, "codes": codes, "q": q}
+        out["cpu_baseline"] = cpu_baseline(w, L, 1000)
+    ix.close()
+    out["seconds_total"] = round(time.time() - t_all, 1)
+    return out
+
+
 def cpu_baseline(w, L: int, sample: int):
     """The CPU oracle as it stands (synchronous search, every host core) on the
     first `sample` queries of the same workload and index."""
@@ -563,6 +673,11 @@ def main():
                     help="only run the precision workload (float32 DEEP-like, BF16/FP8/PQ navigation)")
     ap.add_argument("--precision-n", type=int, default=10_000_000)
     ap.add_argument("--precision-Ls", type=int, nargs="+", default=[32, 64, 128, 256, 512])
+    ap.add_argument("--large", action="store_true",
+                    help="only run the large out-of-core workload (10^8 uint8 vectors by default)")
+    ap.add_argument("--large-n", type=int, default=100_000_000)
+    ap.add_argument("--large-L", type=int, default=128)
+    ap.add_argument("--large-Lb", type=int, default=128, help="L_build of the large index")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only print the storage-tier probe's GB/s for several read sizes")
     args = ap.parse_args()
@@ -570,6 +685,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.precision:
         print(json.dumps(run_precision(args)), flush=True)
+        return
+    if args.large:
+        print(json.dumps(run_large(args)), flush=True)
         return
     if args.probe_sweep:
         import paper_2507_10070_b300 as ann
