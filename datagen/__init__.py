@@ -15,7 +15,7 @@ mixture component, d for its d normals), so the output does not depend on the
 chunk size used to generate it.
 
 Streams: 0 centres, 1 base vectors, 2 queries, 3 PQ training randomness,
-4 graph-build randomness.  Workload seeds are 2507_10070 + workload number.
+4 graph-build randomness, 5 random-link graphs, 6 random bytes.  Workload seeds are 2507_10070 + workload number.
 
 Because the generator is counter-based, any run of vectors can be drawn on
 its own (the stream jumps to draw i*(d+1)); large bases are generated in
@@ -36,6 +36,8 @@ STREAM_BASE = 1
 STREAM_QUERIES = 2
 STREAM_PQ = 3
 STREAM_BUILD = 4
+STREAM_LINKS = 5
+STREAM_BYTES = 6
 
 _CHUNK = 1 << 16
 
@@ -112,12 +114,7 @@ class Mixture:
     def _draw(self, stream: int, n: int, workers: int | None = None) -> np.ndarray:
         assert self.d % 2 == 0, "Box-Muller pairs need an even dimension"
         dtype = np.uint8 if self.kind == "u8" else np.float32
-        workers = workers if workers is not None else (os.cpu_count() or 1)
-        if n >= 4 * _PAR_ROWS and workers > 1:
-            return _draw_parallel(self, stream, n, dtype, workers)
-        out = np.empty((n, self.d), dtype=dtype)
-        self._draw_rows(stream, 0, n, out)
-        return out
+        return _rows(_mixture_rows, (self, stream), n, self.d, dtype, workers)
 
     def base(self, n: int, workers: int | None = None) -> np.ndarray:
         return self._draw(STREAM_BASE, n, workers)
@@ -129,35 +126,86 @@ class Mixture:
 _PAR_ROWS = 1 << 20  # rows per worker task
 
 
+def _mixture_rows(mixture, stream, lo, hi, out):
+    mixture._draw_rows(stream, lo, hi, out)
+
+
+def _link_rows(seed, n, R, lo, hi, out):
+    """Rows [lo, hi) of a random-link graph: R ids uniform in [0, n) per row
+    (draw i*R + j is row i's j-th id); repeats and self links are kept."""
+    s = Stream(seed, STREAM_LINKS, position=lo * R)
+    for a in range(lo, hi, _CHUNK):
+        m = min(_CHUNK, hi - a)
+        out[a - lo:a - lo + m] = (s.uniform((m, R)) * n).astype(np.int32)
+
+
+def _byte_rows(seed, width, lo, hi, out):
+    """Rows [lo, hi) of uniform random bytes, width/8 raw 64-bit draws per row
+    (little-endian byte order)."""
+    s = Stream(seed, STREAM_BYTES, position=lo * (width // 8))
+    for a in range(lo, hi, _CHUNK):
+        m = min(_CHUNK, hi - a)
+        out[a - lo:a - lo + m] = s.raw(m * width // 8).view(np.uint8).reshape(m, width)
+
+
 def _fill_task(args):
     from multiprocessing import shared_memory
-    mixture, stream, lo, hi, name, n, dtype = args
+    fn, fn_args, lo, hi, name, n, width, dtype = args
     shm = shared_memory.SharedMemory(name=name)
     try:
-        arr = np.ndarray((n, mixture.d), dtype=dtype, buffer=shm.buf)
-        mixture._draw_rows(stream, lo, hi, arr[lo:hi])
+        arr = np.ndarray((n, width), dtype=dtype, buffer=shm.buf)
+        fn(*fn_args, lo, hi, arr[lo:hi])
     finally:
         shm.close()
     return hi - lo
 
 
-def _draw_parallel(mixture, stream, n, dtype, workers):
-    """Rows drawn by worker processes (spawned, so safe after CUDA is up)
-    into shared memory; identical to the sequential draw."""
+def _shm_free() -> int:
+    """Free bytes of the shared-memory file system (0 if unknown): a slice
+    that does not fit is drawn sequentially instead."""
+    try:
+        st = os.statvfs("/dev/shm")
+        return st.f_bavail * st.f_frsize
+    except OSError:
+        return 0
+
+
+def _rows(fn, fn_args, n, width, dtype, workers=None):
+    """An (n, width) array whose rows [lo, hi) are fn(*fn_args, lo, hi, out).
+    From 4M rows up, worker processes (spawned, so safe after CUDA is up) fill
+    1M-row slices of shared memory; the result equals the sequential fill
+    because every generator here jumps its counter to the slice's first row."""
+    workers = workers if workers is not None else (os.cpu_count() or 1)
+    nbytes = n * width * np.dtype(dtype).itemsize
+    if n < 4 * _PAR_ROWS or workers <= 1 or _shm_free() < nbytes + (1 << 30):
+        out = np.empty((n, width), dtype=dtype)
+        fn(*fn_args, 0, n, out)
+        return out
     import multiprocessing as mp
     from multiprocessing import shared_memory
-    nbytes = n * mixture.d * np.dtype(dtype).itemsize
     shm = shared_memory.SharedMemory(create=True, size=max(nbytes, 1))
     try:
-        tasks = [(mixture, stream, lo, min(n, lo + _PAR_ROWS), shm.name, n, dtype)
+        tasks = [(fn, fn_args, lo, min(n, lo + _PAR_ROWS), shm.name, n, width, dtype)
                  for lo in range(0, n, _PAR_ROWS)]
         with mp.get_context("spawn").Pool(min(workers, len(tasks))) as pool:
             assert sum(pool.map(_fill_task, tasks)) == n
-        out = np.ndarray((n, mixture.d), dtype=dtype, buffer=shm.buf).copy()
+        out = np.ndarray((n, width), dtype=dtype, buffer=shm.buf).copy()
     finally:
         shm.close()
         shm.unlink()
     return out
+
+
+def random_links(seed: int, n: int, R: int, workers: int | None = None) -> np.ndarray:
+    """n x R int32 random-link graph (uniform ids with repeats and self links),
+    as used for sample indices whose I/O pattern, not quality, matters."""
+    return _rows(_link_rows, (seed, n, R), n, R, np.int32, workers)
+
+
+def random_bytes(seed: int, n: int, width: int, workers: int | None = None) -> np.ndarray:
+    """n x width uint8 of uniform random bytes (width a multiple of 8)."""
+    assert width % 8 == 0
+    return _rows(_byte_rows, (seed, width), n, width, np.uint8, workers)
 
 
 def inmemory_f32(seed_offset: int = 1, d: int = 128, n_centres: int = 32) -> Mixture:
@@ -167,6 +215,11 @@ def inmemory_f32(seed_offset: int = 1, d: int = 128, n_centres: int = 32) -> Mix
 
 def sift_like(seed_offset: int = 2, d: int = 128, n_centres: int = 256) -> Mixture:
     """SIFT-like uint8 workload: centres in [0,255]^d, sigma 20, clipped, rounded."""
+    return Mixture(SEED_BASE + seed_offset, d, n_centres, 0.0, 255.0, 20.0, "u8")
+
+
+def sift_like_large(seed_offset: int = 5, d: int = 128, n_centres: int = 4096) -> Mixture:
+    """The SIFT-like generator with 4,096 centres, for the 10^8-vector workload."""
     return Mixture(SEED_BASE + seed_offset, d, n_centres, 0.0, 255.0, 20.0, "u8")
 
 

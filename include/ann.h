@@ -297,6 +297,16 @@ int ann_build_pq(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t 
                  float* codebook_out, uint8_t* codes_out, int32_t nthreads);
 
 /*
+ * PQ encoding on the GPU (index-construction tooling): the code of every
+ * vector and subspace is its nearest centroid, lowest index on ties -- the
+ * same codes as ann_build_pq's encoder.  uint8 data with an integer
+ * codebook in [0,255] (as ann_build_pq trains for uint8), (d/M) % 4 == 0.
+ * base, codebook, codes_out: host buffers.  Uses the current device.
+ */
+int ann_pq_encode_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t M,
+                      const float* codebook, uint8_t* codes_out);
+
+/*
  * Build a Vamana graph (index-construction tooling; host threads).  Random
  * out-neighbours to start, then two passes (alpha 1, then `alpha`) of
  * GreedySearch(entry, x_p, L_build) + RobustPrune + back edges over a random

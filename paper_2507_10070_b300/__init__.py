@@ -234,14 +234,24 @@ class Server:
 
 
 def build_pq(base, M: int, n_train: int = 100_000, iters: int = 25, kpp_uniforms=None,
-             seed: int = 0, threads: int = 0):
-    """Train a PQ codebook on the first n_train rows and encode every row.
+             seed: int = 0, threads: int = 0, encode_device: str = "cpu"):
+    """Train a PQ codebook on the first n_train rows and encode every row
+    (host threads, or the GPU for uint8 data with encode_device="gpu").
     Returns (codebook float32 (M,256,d/M), codes uint8 (n,M))."""
     base = _c(base)
     n, d = base.shape
     cb = np.empty((M, 256, d // M), np.float32)
-    codes = np.empty((n, M), np.uint8)
     u = None if kpp_uniforms is None else _c(kpp_uniforms, np.float64)
+    if encode_device == "gpu":
+        ns = min(n, n_train)
+        sample = np.ascontiguousarray(base[:ns])
+        scratch = np.empty((ns, M), np.uint8)
+        _check(_lib().ann_build_pq(_p(sample), _dtype_code(base), ns, d, M, n_train, iters, _p(u),
+                                   ctypes.c_uint64(seed), _p(cb), _p(scratch), threads))
+        codes = np.empty((n, M), np.uint8)
+        _check(_lib().ann_pq_encode_gpu(_p(base), _dtype_code(base), n, d, M, _p(cb), _p(codes)))
+        return cb, codes
+    codes = np.empty((n, M), np.uint8)
     _check(_lib().ann_build_pq(_p(base), _dtype_code(base), n, d, M, n_train, iters, _p(u),
                                ctypes.c_uint64(seed), _p(cb), _p(codes), threads))
     return cb, codes

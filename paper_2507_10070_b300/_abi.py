@@ -22,7 +22,8 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
-           "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3"]
+           "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3",
+           "ann_pq_encode_gpu"]
 
 
 class AnnError(RuntimeError):
@@ -128,6 +129,8 @@ def lib():
         L.ann_encode_bf16.argtypes = [P, I64, P]
         L.ann_encode_fp8e4m3.restype = ctypes.c_int
         L.ann_encode_fp8e4m3.argtypes = [P, I64, ctypes.c_float, P]
+        L.ann_pq_encode_gpu.restype = ctypes.c_int
+        L.ann_pq_encode_gpu.argtypes = [P, I32, I64, I32, I32, P, P]
         L.ann_knn_exact.restype = ctypes.c_int
         L.ann_knn_exact.argtypes = [P, I32, I64, I32, P, I64, I32, P, P]
         L.ann_probe_read_bandwidth.restype = ctypes.c_int

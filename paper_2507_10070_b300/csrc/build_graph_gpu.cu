@@ -3,7 +3,10 @@
 // host builder (build_graph.cpp): random start graph, one pass with alpha = 1
 // and one with `alpha`, nodes inserted in batches that grow geometrically up
 // to 2% of n, every search of a batch reading the graph as it stood before
-// the batch.
+// the batch.  The start graph and the insertion order are drawn on the device
+// from a counter-based generator (node i's draws depend only on the seed and
+// i), so they take no host time or host copy of the graph at 10^8 nodes; they
+// are therefore other random draws than the host builder's.
 //
 // Per batch:
 //  1. gather the batch's vectors;
@@ -36,11 +39,49 @@ namespace {
 constexpr int kCandMax = 256;  // candidates one prune task considers
 constexpr unsigned kFull = 0xffffffffu;
 
-uint64_t splitmix64(uint64_t& s) {
-  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+constexpr uint64_t kGolden = 0x9e3779b97f4a7c15ull;
+
+// splitmix64's output function (Steele, Lea and Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
   return z ^ (z >> 31);
+}
+
+// Start graph: node i draws init_deg distinct out-neighbours != i from its own
+// splitmix64 sequence, started at seed ^ mix64(i + 1).  The rejection loop is
+// capped; past the cap (only reachable when init_deg is close to n - 1) the
+// row is completed by a scan in id order.
+__global__ void random_rows(int64_t n, int init_deg, uint64_t seed, int32_t* __restrict__ adj,
+                            int stride) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t* row = adj + static_cast<size_t>(i) * stride;
+  uint64_t s = seed ^ mix64(static_cast<uint64_t>(i) + 1);
+  int c = 0;
+  for (int it = 0; c < init_deg && it < 64 * init_deg + 1024; ++it) {
+    s += kGolden;
+    const int32_t v = static_cast<int32_t>(mix64(s) % static_cast<uint64_t>(n));
+    bool dup = v == i;
+    for (int j = 0; j < c; ++j) dup |= row[j] == v;
+    if (!dup) row[c++] = v;
+  }
+  for (int64_t v = 0; c < init_deg && v < n; ++v) {
+    bool dup = v == i;
+    for (int j = 0; j < c; ++j) dup |= row[j] == v;
+    if (!dup) row[c++] = static_cast<int32_t>(v);
+  }
+  for (int j = c; j < stride; ++j) row[j] = -1;
+}
+
+// Insertion order: nodes sorted by a per-node 64-bit hash (ties by id, the
+// sort being stable), i.e. a uniformly random permutation.
+__global__ void order_keys(int64_t n, uint64_t seed, unsigned long long* __restrict__ key,
+                           int32_t* __restrict__ id) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  key[i] = mix64(mix64(seed ^ 0x5851f42d4c957f2dull) + static_cast<uint64_t>(i) * kGolden);
+  id[i] = static_cast<int32_t>(i);
 }
 
 __global__ void gather_rows(const uint8_t* __restrict__ base, int row_bytes,
@@ -293,25 +334,7 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
         entry = bi[t];
       }
   }
-  // random start graph and insertion order (host), as the host builder
-  std::vector<int32_t> adj((size_t)n * stride, -1);
-  uint64_t rs = seed;
   const int init_deg = static_cast<int>(std::min<int64_t>(R, n - 1));
-  for (int64_t i = 0; i < n; ++i) {
-    int32_t* row = &adj[(size_t)i * stride];
-    int c = 0;
-    while (c < init_deg) {
-      const int32_t v = static_cast<int32_t>(splitmix64(rs) % static_cast<uint64_t>(n));
-      if (v == i) continue;
-      bool dup = false;
-      for (int j = 0; j < c; ++j) dup |= row[j] == v;
-      if (!dup) row[c++] = v;
-    }
-  }
-  std::vector<int32_t> order(n);
-  for (int64_t i = 0; i < n; ++i) order[i] = static_cast<int32_t>(i);
-  for (int64_t i = n - 1; i > 0; --i) std::swap(order[i], order[splitmix64(rs) % static_cast<uint64_t>(i + 1)]);
-
   const int64_t max_batch = std::max<int64_t>(1, n / 50);
   const int mode = dtype == ANN_U8 ? kModeExactU8 : kModeExactF32;
   const int pool = std::min(L_build + 64, kCandMax - R);  // results kept per search
@@ -347,10 +370,35 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   } while (0)
   GB_TRY(dmalloc(&base_d, (size_t)n * row_bytes), "cudaMalloc vectors");
   GB_TRY(cudaMemcpy(base_d, base, (size_t)n * row_bytes, cudaMemcpyHostToDevice), "upload vectors");
-  GB_TRY(dmalloc(&adj_d, adj.size()), "cudaMalloc adjacency");
-  GB_TRY(cudaMemcpy(adj_d, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice), "upload adjacency");
+  // random start graph and insertion order, on the device
+  const unsigned gn = static_cast<unsigned>((n + 255) / 256);
+  GB_TRY(dmalloc(&adj_d, (size_t)n * stride), "cudaMalloc adjacency");
+  random_rows<<<gn, 256>>>(n, init_deg, seed, adj_d, stride);
   GB_TRY(dmalloc(&order_d, (size_t)n), "cudaMalloc order");
-  GB_TRY(cudaMemcpy(order_d, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice), "upload order");
+  {
+    unsigned long long *k0 = nullptr, *k1 = nullptr;
+    int32_t* i0 = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    e = dmalloc(&k0, (size_t)n);
+    if (e == cudaSuccess) e = dmalloc(&k1, (size_t)n);
+    if (e == cudaSuccess) e = dmalloc(&i0, (size_t)n);
+    if (e == cudaSuccess) {
+      order_keys<<<gn, 256>>>(n, seed, k0, i0);
+      e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k0, k1, i0, order_d, (int)n);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, std::max<size_t>(tmp_bytes, 1));
+    if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, i0, order_d, (int)n);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(k0);
+    cudaFree(k1);
+    cudaFree(i0);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_error(e, "start graph / insertion order");
+    }
+  }
   GB_TRY(dmalloc(&qbuf, (size_t)max_batch * row_bytes), "cudaMalloc batch");
   GB_TRY(dmalloc(&cand_ids, (size_t)max_batch * pool), "cudaMalloc candidates");
   GB_TRY(dmalloc(&cand_d, (size_t)max_batch * pool), "cudaMalloc candidates");
@@ -448,10 +496,8 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
     }
   }
   GB_TRY(cudaStreamSynchronize(st), "build");
-  std::vector<int32_t> rows((size_t)n * stride);
-  GB_TRY(cudaMemcpy(rows.data(), adj_d, rows.size() * 4, cudaMemcpyDeviceToHost), "download adjacency");
-  for (int64_t i = 0; i < n; ++i)
-    std::memcpy(adj_out + (size_t)i * R, rows.data() + (size_t)i * stride, (size_t)R * 4);
+  GB_TRY(cudaMemcpy2D(adj_out, (size_t)R * 4, adj_d, (size_t)stride * 4, (size_t)R * 4, (size_t)n,
+                      cudaMemcpyDeviceToHost), "download adjacency");
   if (entry_out) *entry_out = (int32_t)entry;
   cleanup();
 #undef GB_TRY

@@ -60,3 +60,25 @@ def test_parallel_generation_equals_sequential():
         mx._draw_rows(datagen.STREAM_BASE, lo, lo + 5, chunk)
         assert np.array_equal(par[lo:lo + 5], chunk)
     assert np.array_equal(par[:70_000], mx.base(70_000, workers=1))
+
+
+def test_random_links_and_bytes():
+    n = 4 * datagen._PAR_ROWS + 77
+    g = datagen.random_links(9, n, 4, workers=4)                # parallel path
+    assert g.shape == (n, 4) and g.dtype == np.int32
+    assert g.min() >= 0 and g.max() < n
+    assert np.array_equal(g[:50_000], datagen.random_links(9, n, 4, workers=1)[:50_000])
+    tail = np.empty((77, 4), np.int32)
+    datagen._link_rows(9, n, 4, n - 77, n, tail)                 # counter jump to the tail
+    assert np.array_equal(g[-77:], tail)
+    # roughly uniform: each quarter of the id range gets a quarter of the links
+    frac = np.bincount(g.ravel() // (n // 4 + 1), minlength=4) / g.size
+    assert np.all(np.abs(frac - 0.25) < 0.001)
+    small = datagen.random_links(9, 1000, 64)
+    assert any(len(set(r.tolist())) < 64 for r in small)          # repeats are kept
+    b = datagen.random_bytes(3, 1000, 16)
+    assert b.shape == (1000, 16) and b.dtype == np.uint8
+    part = np.empty((10, 16), np.uint8)
+    datagen._byte_rows(3, 16, 500, 510, part)
+    assert np.array_equal(b[500:510], part)
+    assert abs(b.mean() - 127.5) < 2.0

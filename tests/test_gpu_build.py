@@ -68,3 +68,12 @@ def test_gpu_build_rejects_bad_sizes():
         ann.build_graph(x, 16, device="gpu")                 # d % 16 != 0
     with pytest.raises(ann.AnnError):
         ann.build_graph(np.zeros((100, 16), np.uint8), 96, L_build=128, device="gpu")   # R > 64
+
+
+def test_gpu_pq_encoder_equals_host_encoder():
+    mx = datagen.sift_like()
+    base = mx.base(50_000)
+    u = datagen.kmeanspp_uniforms(mx.seed, 32)
+    cb, codes = ann.build_pq(base, 32, n_train=5000, iters=4, kpp_uniforms=u)
+    cb2, codes2 = ann.build_pq(base, 32, n_train=5000, iters=4, kpp_uniforms=u, encode_device="gpu")
+    assert np.array_equal(cb, cb2) and np.array_equal(codes, codes2)

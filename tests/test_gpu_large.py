@@ -1,0 +1,74 @@
+"""Out-of-core search at 10^8 nodes: 51.2 GB of 512-byte node blocks in host
+pinned memory, 3.2 GB of PQ codes in HBM, 10,000 queries in one batch at
+L=128 and depths 0 and 1.  Sampled queries must match the oracle bit-exactly
+(ids, distances, step counts); every query must give sorted distances equal
+to the exact integer L2 of its ids.
+
+The index is a random-link sample index (R=64 uniform neighbour ids, uniform
+random uint8 vectors and PQ codes, an integer codebook), the kind the degree
+selector measures: its I/O pattern is the workload's, and the oracle can take
+it as input because it comes from the seeded generators, not from CUDA code.
+Node ids reach 10^8 and block addresses pass 2^32 bytes.
+
+Needs ~100 GB of host memory and a few minutes of setup, so it runs only with
+ANN_LARGE_TEST=1 (ANN_LARGE_N overrides the number of nodes).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2507_10070_b300 as ann
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("ANN_LARGE_TEST") != "1",
+                                 reason="10^8-node test: set ANN_LARGE_TEST=1")]
+
+N = int(os.environ.get("ANN_LARGE_N", 100_000_000))
+NQ, R, M, D = 10_000, 64, 32, 128
+SAMPLE = np.r_[0:24, 5000:5016, NQ - 24:NQ]
+
+
+@pytest.fixture(scope="module")
+def large():
+    seed = datagen.SEED_BASE + 50
+    base = datagen.random_bytes(seed, N, D)
+    adj = datagen.random_links(seed, N, R)
+    codes = datagen.random_bytes(seed + 1, N, M)
+    cb = np.floor(datagen.Stream(seed, datagen.STREAM_PQ).uniform((M, 256, D // M)) * 256)
+    cb = cb.astype(np.float32)
+    q = datagen.random_bytes(seed + 2, NQ, D)
+    ix = ann.Index(base, adj, 0, cb, codes, tier=ann.ANN_TIER_HOST_PINNED)
+    yield dict(base=base, adj=adj, codes=codes, cb=cb, q=q, ix=ix)
+    ix.close()
+
+
+@pytest.mark.parametrize("depth", [1, 0])
+def test_large_batch_against_oracle(large, depth):
+    import torch
+    w = large
+    k, L = 10, 128
+    q = torch.from_numpy(w["q"]).cuda()
+    ids = torch.empty((NQ, k), dtype=torch.int32, device="cuda")
+    dists = torch.empty((NQ, k), dtype=torch.float32, device="cuda")
+    steps = torch.empty(NQ, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    w["ix"].search_dev(q, k, L, depth, ids, dists, stream=st, trace={"steps": steps})
+    stats = w["ix"].sync(st)
+    assert stats.n_failed == 0
+    ids, dists, steps = ids.cpu().numpy(), dists.cpu().numpy(), steps.cpu().numpy()
+    oi, od, os_ = oracle.search(w["base"], w["adj"], 0, w["q"][SAMPLE], k, L, depth,
+                                codebook=w["cb"], codes=w["codes"])
+    assert np.array_equal(ids[SAMPLE], oi)
+    assert np.array_equal(dists[SAMPLE].astype(np.float64), od)
+    assert np.array_equal(steps[SAMPLE], os_)
+    assert np.all(ids >= 0) and np.all(np.diff(dists, axis=1) >= 0)
+    for lo in range(0, NQ, 1000):          # exact distances of every returned id
+        x = w["base"][ids[lo:lo + 1000]].astype(np.int32)
+        ex = ((x - w["q"][lo:lo + 1000, None, :].astype(np.int32)) ** 2).sum(-1)
+        assert np.array_equal(dists[lo:lo + 1000].astype(np.int64), ex)
+    assert stats.expansions == int(steps.sum())
+    if N >= 2 ** 27:
+        assert ids.max() >= 2 ** 26

@@ -187,6 +187,26 @@ def test_degenerate_graphs():
         one.close()
 
 
+@pytest.mark.parametrize("L,depth", [(16, 0), (128, 2)])
+def test_repeated_ids_and_self_links(u8_pq, L, depth):
+    """Rows with repeated neighbour ids and self links (a random-link graph
+    folded onto 400 ids): a repeat is seen as visited, as in the oracle."""
+    w = u8_pq
+    n = 3000
+    base = w["base"][:n]
+    adj = datagen.random_links(1, n, 64) % 400
+    codes = np.ascontiguousarray(w["codes"][:n])
+    assert any(len(set(r.tolist())) < 64 for r in adj) and any(i in adj[i] for i in range(400))
+    ix = ann.Index(base, adj, 7, w["cb"], codes, tier=ann.ANN_TIER_HOST_PINNED)
+    try:
+        ids, d, _, tr = ix.search(w["q"], 10, L, depth, trace=True)
+    finally:
+        ix.close()
+    oi, od, os_ = oracle.search(base, adj, 7, w["q"], 10, L, depth, codebook=w["cb"], codes=codes)
+    assert np.array_equal(ids, oi) and np.array_equal(d.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
 def test_visited_overflow_reports_enomem():
     """The device's failure path, checked from the host: on a ring lattice
     (node i -> i+1..i+R, positions on a line) a query at the far end makes the
