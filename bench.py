@@ -271,6 +271,20 @@ def run_ours(args, rank: int, world: int):
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
 
+    # ---- ablation: kernel-grained I/O (grid barrier after every fetch wait), depth 0
+    kg_ms = []
+    for i in range(args.warmup + 3):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.search_dev_kernel_grained(qd, k, chosen_L, 0, ids, dists, stream=stream)
+        e1.record(stream)
+        ix.sync(stream)
+        if i >= args.warmup:
+            kg_ms.append(e0.elapsed_time(e1))
+    kg_qps = nq / (float(np.median(kg_ms)) * 1e-3)
+
     # ---- roofline of the search kernel (storage-tier bound)
     bytes_per_launch = st.expansions / args.steps * st.bytes_per_expansion
     achieved = bytes_per_launch / (total_ms / args.steps * 1e-3) / 1e9
@@ -289,6 +303,11 @@ def run_ours(args, rank: int, world: int):
         "sync": {"value": round(qps_sync, 1), "ms_per_step": round(float(np.mean(ms_sync)), 4),
                  "mean_steps": round(st_sync.expansions / max(st_sync.queries, 1), 2)},
         "relaxed_mean_steps": round(st.expansions / max(st.queries, 1), 2),
+        "ablation_io_granularity": {
+            "what": "kernel-grained I/O (CAM-style: every resident warp waits at a grid barrier after each fetch) against the query-grained synchronous search, same L, depth 0",
+            "kernel_grained_qps": round(kg_qps, 1), "query_grained_sync_qps": round(qps_sync, 1),
+            "query_grained_relaxed_qps": round(qps / world, 1),
+            "query_over_kernel_grained": round(qps_sync / kg_qps, 3)},
         "relaxed_over_sync": round(qps / world / qps_sync, 4),
         "latency_us": {"p50": round(float(np.percentile(lat_us, 50)), 1),
                        "p99": round(float(np.percentile(lat_us, 99)), 1),
@@ -497,12 +516,17 @@ def run_large(args):
     4,096 Gaussians, otherwise as the 1M workload), 10^8 of them by default;
     Vamana R=64 built by the library's GPU tooling off the clock; 32-byte PQ
     codes in HBM (3.2 GB at 10^8); 512-byte node blocks in host pinned memory
-    (51.2 GB at 10^8); 10,000 queries, k=10, L=128.  Each depth of the
-    pipeline is timed on the batched search (queries resident in HBM, L2
-    flushed between steps); the relaxed pipeline is reported at the fastest
-    depth > 0, next to the synchronous search (depth 0), and the serving loop
-    runs on the same index.  Recall@10 is against exact GPU ground truth; the
-    returned distances of a sample are checked against exact integer L2."""
+    (51.2 GB at 10^8); 10,000 queries, k=10, L=128.  The index is timed in
+    two storage orders of the node blocks: the build's (node ids as
+    generated) and breadth-first from the entry node (ann_reorder_graph,
+    results mapped back to the original ids by the index's id map), which
+    keeps a query's successive fetches in the same 64 KB translation pages.
+    Each depth of the pipeline is timed on the batched search (queries
+    resident in HBM, L2 flushed between steps); the relaxed pipeline is
+    reported at the fastest depth > 0 of the breadth-first layout, next to
+    the synchronous search (depth 0), and the serving loop runs on that
+    index.  Recall@10 is against exact GPU ground truth; the returned
+    distances of a sample are checked against exact integer L2."""
     import torch
     import paper_2507_10070_b300 as ann
     torch.cuda.set_device(0)
@@ -524,18 +548,15 @@ def run_large(args):
     t = time.time()
     gt_ids, gt_d = ann.knn_exact(base, q, k)
     prep["ground_truth_s"] = round(time.time() - t, 1)
-    probe_1g = ann.probe_read_bandwidth(1 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
-    probe_16g = ann.probe_read_bandwidth(16 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
-    t = time.time()
-    ix = ann.Index(base, adj, entry, cb, codes, tier=ann.ANN_TIER_HOST_PINNED)
-    prep["index_load_s"] = round(time.time() - t, 1)
+    probe = {f"{g}GiB_region": round(ann.probe_read_bandwidth(g << 30, 384, ann.ANN_TIER_HOST_PINNED, 64), 2)
+             for g in (1, 16)}
     qd = torch.from_numpy(q).to(dev)
     ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
     dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
 
-    def timed(depth, K, W):
+    def timed(ix, depth, K, W):
         for _ in range(W):
             ix.search_dev(qd, k, L, depth, ids, dists, stream=stream)
         ix.sync(stream)
@@ -552,17 +573,34 @@ def run_large(args):
         torch.cuda.synchronize()
         return float(np.sum([a.elapsed_time(b) for a, b in ev])), st
 
-    by_depth = {}
-    with ClockSampler(0) as clk:
-        for depth in (0, 1, 2, 4):
-            ms, st = timed(depth, args.steps, args.warmup)
+    def sweep(ix, depths):
+        rows = {}
+        for depth in depths:
+            ms, st = timed(ix, depth, args.steps, args.warmup)
             hi, hd = ids.cpu().numpy(), dists.cpu().numpy()
-            by_depth[depth] = {
+            rows[depth] = {
                 "qps": round(nq * args.steps / (ms * 1e-3), 1),
                 "ms_per_step": round(ms / args.steps, 3),
                 "recall_at_10": round(ann.recall_at_k(hi, gt_ids, gt_d, hd), 4),
                 "mean_steps": round(st.expansions / max(st.queries, 1), 2),
                 "pcie_gbs": round(st.expansions * st.bytes_per_expansion / (ms * 1e-3) / 1e9, 2)}
+        return rows
+
+    # ---- storage order of the build (node ids as generated)
+    t = time.time()
+    ix = ann.Index(base, adj, entry, cb, codes, tier=ann.ANN_TIER_HOST_PINNED)
+    prep["index_load_s"] = round(time.time() - t, 1)
+    with ClockSampler(0) as clk_a:
+        build_order = sweep(ix, (0, 1))
+    ix.close()
+    # ---- breadth-first storage order
+    t = time.time()
+    b2, a2, e2, c2, old = ann.reorder_graph(base, adj, entry, codes)
+    prep["reorder_s"] = round(time.time() - t, 1)
+    del adj, codes
+    ix = ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
+    with ClockSampler(0) as clk:
+        by_depth = sweep(ix, (0, 1, 2, 4))
     best = max((1, 2, 4), key=lambda d: by_depth[d]["qps"])
     ix.search_dev(qd, k, L, best, ids, dists, stream=stream)
     ix.sync(stream)
@@ -571,7 +609,8 @@ def run_large(args):
     x = base[hi[s]].astype(np.int64)
     exact = ((x - q[s][:, None, :].astype(np.int64)) ** 2).sum(-1)
     checks = {"sampled_queries": int(s.size),
-              "distances_equal_exact_l2": bool(np.array_equal(hd[s].astype(np.int64), exact)),
+              "ids_valid": bool(np.all((hi >= 0) & (hi < n))),
+              "distances_equal_exact_l2_of_original_ids": bool(np.array_equal(hd[s].astype(np.int64), exact)),
               "ids_distinct": bool(all(len(set(r.tolist())) == k for r in hi)),
               "distances_sorted": bool(np.all(np.diff(hd, axis=1) >= 0))}
     out = {"what": run_large.__doc__.split("\n\n")[0].replace("\n", " "),
@@ -579,17 +618,25 @@ def run_large(args):
            "host_pinned_node_blocks_gb": round(n * ix.block_bytes / 1e9, 1),
            "hbm_pq_codes_gb": round(n * M / 1e9, 2),
            "value": by_depth[best]["qps"], "unit": "queries/s", "depth": best,
+           "layout": "breadth-first from the entry node (id map back to the original ids)",
            "recall_at_10": by_depth[best]["recall_at_10"],
            "sync": by_depth[0], "relaxed_over_sync": round(by_depth[best]["qps"] / by_depth[0]["qps"], 4),
            "by_depth": {str(d): v for d, v in by_depth.items()},
-           "probe_gbs_384B": {"1GiB_region": round(probe_1g, 2), "16GiB_region": round(probe_16g, 2)},
-           "checks": checks, "prep": prep, "clocks": clk.summary()}
+           "build_order_by_depth": {str(d): v for d, v in build_order.items()},
+           "breadth_first_over_build_order": round(by_depth[1]["qps"] / build_order[1]["qps"], 3),
+           "probe_gbs_384B": probe, "checks": checks, "prep": prep,
+           "clocks": clk.summary(), "clocks_build_order": clk_a.summary()}
     if args.serve_seconds > 0:
         out["serving"] = run_serving(ix, {"q": q}, gt_ids, gt_d, L, best, args.serve_seconds)
-    if not args.no_cpu_baseline:
-        w = {"base": base, "adj": adj, "entry": entry, "cb": cb, "codes": codes, "q": q}
-        out["cpu_baseline"] = cpu_baseline(w, L, 1000)
     ix.close()
+    # context: the same breadth-first index with the node blocks in HBM
+    ixh = ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HBM, id_map=old)
+    out["hbm_tier_context"] = {"what": "the same index with its node blocks in HBM instead of host memory",
+                               "by_depth": {str(d): v for d, v in sweep(ixh, (0, 1)).items()}}
+    ixh.close()
+    if not args.no_cpu_baseline:
+        w = {"base": b2, "adj": a2, "entry": e2, "cb": cb, "codes": c2, "q": q}
+        out["cpu_baseline"] = cpu_baseline(w, L, 1000)
     out["seconds_total"] = round(time.time() - t_all, 1)
     return out
 

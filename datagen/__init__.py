@@ -182,13 +182,17 @@ def _rows(fn, fn_args, n, width, dtype, workers=None):
         fn(*fn_args, 0, n, out)
         return out
     import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
     from multiprocessing import shared_memory
     shm = shared_memory.SharedMemory(create=True, size=max(nbytes, 1))
     try:
         tasks = [(fn, fn_args, lo, min(n, lo + _PAR_ROWS), shm.name, n, width, dtype)
                  for lo in range(0, n, _PAR_ROWS)]
-        with mp.get_context("spawn").Pool(min(workers, len(tasks))) as pool:
-            assert sum(pool.map(_fill_task, tasks)) == n
+        # an executor (not a Pool) so that a worker that dies -- e.g. a script
+        # without a __main__ guard re-running itself under spawn -- fails the
+        # call at once instead of being respawned forever
+        with ProcessPoolExecutor(min(workers, len(tasks)), mp_context=mp.get_context("spawn")) as ex:
+            assert sum(ex.map(_fill_task, tasks)) == n
         out = np.ndarray((n, width), dtype=dtype, buffer=shm.buf).copy()
     finally:
         shm.close()

@@ -93,6 +93,10 @@ typedef struct {
   int32_t nav;           /* ann_nav (0 = ANN_NAV_AUTO) */
   float nav_scale;       /* ANN_NAV_FP8: values are encoded as x * nav_scale (> 0) */
   int32_t rerank_mult;   /* precision variants: rerank the top rerank_mult*k (0 means 4) */
+  const int32_t* id_map; /* NULL, or n ids: the caller's id of each stored node.  Searches
+                            report id_map[node] instead of the node's position (any int32
+                            values; -1 still pads missing results).  Set by layouts that
+                            store nodes in another order, e.g. ann_reorder_graph's. */
 } ann_graph_desc;
 
 /* Per-query outputs of a search (each pointer may be NULL).  Memory kind as
@@ -100,7 +104,8 @@ typedef struct {
  * ann_search_dev). */
 typedef struct {
   int32_t* steps;   /* [nq] node blocks fetched and expanded (search steps) */
-  int32_t* status;  /* [nq] ANN_OK, or ANN_ENOMEM if the visited set overflowed */
+  int32_t* status;  /* [nq] ANN_OK, ANN_ENOMEM if the visited set overflowed, or
+                       ANN_ETIMEOUT (kernel-grained ablation only) */
   int64_t* t_begin; /* [nq] device global timer (ns) when the query started */
   int64_t* t_end;   /* [nq] device global timer (ns) when it finished */
 } ann_trace;
@@ -137,8 +142,9 @@ const char* ann_version(void);
 int ann_load_graph(ann_index** out, const ann_graph_desc* desc);
 
 /* Write / read an index as one file (header, vectors, adjacency, codebook,
- * codes).  ann_load_graph_file returns ANN_EIO on unreadable or truncated
- * files, then validates like ann_load_graph, placing blocks in `tier`. */
+ * codes, and the id map if the description has one).  ann_load_graph_file
+ * returns ANN_EIO on unreadable or truncated files, then validates like
+ * ann_load_graph, placing blocks in `tier`. */
 int ann_save_graph_file(const char* path, const ann_graph_desc* desc);
 int ann_load_graph_file(ann_index** out, const char* path, int32_t tier);
 
@@ -177,6 +183,22 @@ int ann_search(ann_index* index, const void* queries, int64_t nq, int32_t k, int
 int ann_search_dev(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
                    int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
                    void* stream);
+
+/*
+ * Kernel-grained I/O: the ablation of the paper's query-grained I/O stack
+ * (Section "Resource-Efficient Query-Grained Concurrent I/O Stack", which
+ * compares against CAM, where the kernel waits for every request of the
+ * batch).  Same arguments, kernel and per-query results as ann_search_dev,
+ * but launched cooperatively (every block resident) and with a grid-wide
+ * barrier after each fetch wait: no query expands a node until the fetches
+ * of every resident warp in that round have arrived.  The barrier's waits
+ * are bounded; if one runs out, the queries still running report
+ * ANN_ETIMEOUT and the next ann_sync returns ANN_ETIMEOUT.  For measurement
+ * only -- query-grained I/O (ann_search_dev) is never slower.
+ */
+int ann_search_dev_kernel_grained(ann_index* index, const void* queries, int64_t nq, int32_t k,
+                                  int32_t L, int32_t depth, int32_t* ids, float* dists,
+                                  const ann_trace* trace, void* stream);
 
 /* Wait for `stream`, then report (and reset) the totals and failures of the
  * ann_search_dev calls since the previous ann_sync. */
@@ -305,6 +327,32 @@ int ann_build_pq(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t 
  */
 int ann_pq_encode_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t M,
                       const float* codebook, uint8_t* codes_out);
+
+/*
+ * Storage order of the node blocks (index-construction tooling; host
+ * threads).  The paper places nodes on SSD pages; on this system the
+ * storage tier is host memory that the GPU reads through an address
+ * translation with a 64 KB granule, whose miss rate (about 65 million per
+ * second) caps random 384-byte reads over tens of GB at half the PCIe link.
+ * Storing nodes in breadth-first order from the entry node puts a node and
+ * the neighbours it discovers in the same 64 KB pages, so successive
+ * expansions of a query reuse translations.
+ *
+ * Computes the breadth-first order from `entry` over the rows of `adj`
+ * (neighbours in row order, a row ending at its first -1; when the queue
+ * runs dry, breadth-first again from the lowest id not yet placed) and
+ * writes the index in that order: base_out row i = base row old_of_new[i],
+ * codes_out likewise (codes may be NULL when M == 0), adj_out row i = the
+ * row of old_of_new[i] with every id j replaced by its new position, and
+ * *entry_out = the entry's new position (0).  Load the result with
+ * id_map = old_of_new so that searches report the original ids.  All
+ * buffers are host memory, the outputs disjoint from the inputs.
+ * ANN_EINVAL on bad sizes or ids.
+ */
+int ann_reorder_graph(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                      const int32_t* adj, int32_t entry, const uint8_t* codes, int32_t M,
+                      void* base_out, int32_t* adj_out, uint8_t* codes_out,
+                      int32_t* old_of_new, int32_t* entry_out);
 
 /*
  * Build a Vamana graph (index-construction tooling; host threads).  Random

@@ -54,7 +54,8 @@ def _p(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def _desc(vectors, adj, entry, codebook, codes, tier, nav=0, nav_scale=0.0, rerank_mult=0):
+def _desc(vectors, adj, entry, codebook, codes, tier, nav=0, nav_scale=0.0, rerank_mult=0,
+          id_map=None):
     vectors = _c(vectors)
     adj = _c(adj, np.int32)
     n, d = vectors.shape
@@ -64,16 +65,19 @@ def _desc(vectors, adj, entry, codebook, codes, tier, nav=0, nav_scale=0.0, rera
         codebook = _c(codebook, np.float32)
         codes = _c(codes, np.uint8)
         M = codebook.shape[0]
-    keep = (vectors, adj, codebook, codes)
+    if id_map is not None:
+        id_map = _c(id_map, np.int32)
+        assert id_map.shape == (n,)
+    keep = (vectors, adj, codebook, codes, id_map)
     desc = GraphDesc(n=n, d=d, dtype=_dtype_code(vectors), R=adj.shape[1], entry=int(entry),
                      vectors=_p(vectors), adj=_p(adj), M=M, codebook=_p(codebook),
                      codes=_p(codes), tier=tier, nav=nav, nav_scale=nav_scale,
-                     rerank_mult=rerank_mult)
+                     rerank_mult=rerank_mult, id_map=_p(id_map))
     return desc, keep
 
 
-def save_index(path: str, vectors, adj, entry, codebook=None, codes=None):
-    desc, keep = _desc(vectors, adj, entry, codebook, codes, ANN_TIER_HBM)
+def save_index(path: str, vectors, adj, entry, codebook=None, codes=None, id_map=None):
+    desc, keep = _desc(vectors, adj, entry, codebook, codes, ANN_TIER_HBM, id_map=id_map)
     _check(_lib().ann_save_graph_file(path.encode(), ctypes.byref(desc)))
 
 
@@ -82,7 +86,9 @@ class Index:
 
     def __init__(self, vectors=None, adj=None, entry=0, codebook=None, codes=None,
                  tier: int = ANN_TIER_HOST_PINNED, path: str | None = None, nav: int = 0,
-                 nav_scale: float = 0.0, rerank_mult: int = 0):
+                 nav_scale: float = 0.0, rerank_mult: int = 0, id_map=None):
+        """`id_map` (n int32, optional): the caller's id of each stored node;
+        results report it instead of the node's position (see reorder_graph)."""
         self._h = ctypes.c_void_p()
         if path is not None:
             _check(_lib().ann_load_graph_file(ctypes.byref(self._h), path.encode(), tier))
@@ -91,7 +97,8 @@ class Index:
             fields = hdr[16:40].view(np.int32)
             self.d, self.dtype = int(fields[0]), int(fields[1])
         else:
-            desc, _ = _desc(vectors, adj, entry, codebook, codes, tier, nav, nav_scale, rerank_mult)
+            desc, _ = _desc(vectors, adj, entry, codebook, codes, tier, nav, nav_scale, rerank_mult,
+                            id_map)
             _check(_lib().ann_load_graph(ctypes.byref(self._h), ctypes.byref(desc)))
             self.d, self.dtype = desc.d, desc.dtype
         self.n = int(_lib().ann_index_size(self._h))
@@ -152,6 +159,20 @@ class Index:
                                      ctypes.c_void_p(ids.data_ptr()),
                                      ctypes.c_void_p(dists.data_ptr()),
                                      ctypes.byref(tr) if tr else None, st))
+
+    def search_dev_kernel_grained(self, queries, k: int, L: int, depth: int, ids, dists,
+                                  stream=None, trace: dict | None = None):
+        """search_dev with kernel-grained I/O (the ablation: a grid-wide
+        barrier after every fetch wait; see ann_search_dev_kernel_grained)."""
+        tr = None
+        if trace:
+            tr = Trace(**{key: ctypes.c_void_p(t.data_ptr()) for key, t in trace.items()})
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(_lib().ann_search_dev_kernel_grained(self._h, ctypes.c_void_p(queries.data_ptr()),
+                                                    queries.shape[0], k, L, depth,
+                                                    ctypes.c_void_p(ids.data_ptr()),
+                                                    ctypes.c_void_p(dists.data_ptr()),
+                                                    ctypes.byref(tr) if tr else None, st))
 
     def search_dev_noalloc(self, queries, k: int, L: int, depth: int, ids, dists, stream=None,
                            trace: dict | None = None):
@@ -310,6 +331,27 @@ def encode_fp8e4m3(x, scale: float = 1.0):
     out = np.empty(x.shape, np.uint8)
     _check(_lib().ann_encode_fp8e4m3(_p(x), x.size, ctypes.c_float(scale), _p(out)))
     return out
+
+
+def reorder_graph(base, adj, entry: int, codes=None):
+    """Breadth-first storage order from the entry node (ann_reorder_graph).
+    Returns (base, adj, entry, codes, old_of_new) in the new order; load them
+    with id_map=old_of_new so that searches report the original ids."""
+    base = _c(base)
+    adj = _c(adj, np.int32)
+    n, d = base.shape
+    R = adj.shape[1]
+    M = 0 if codes is None else codes.shape[1]
+    codes = None if codes is None else _c(codes, np.uint8)
+    base_out = np.empty_like(base)
+    adj_out = np.empty_like(adj)
+    codes_out = None if codes is None else np.empty_like(codes)
+    old_of_new = np.empty(n, np.int32)
+    entry_out = ctypes.c_int32(0)
+    _check(_lib().ann_reorder_graph(_p(base), _dtype_code(base), n, d, R, _p(adj), int(entry),
+                                    _p(codes), M, _p(base_out), _p(adj_out), _p(codes_out),
+                                    _p(old_of_new), ctypes.byref(entry_out)))
+    return base_out, adj_out, int(entry_out.value), codes_out, old_of_new
 
 
 def knn_exact(base, queries, k: int):

@@ -19,11 +19,12 @@ STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA"
 EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_file",
            "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
            "ann_search", "ann_search_dev", "ann_sync", "ann_search_dev_noalloc",
+           "ann_search_dev_kernel_grained",
            "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
            "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3",
-           "ann_pq_encode_gpu"]
+           "ann_pq_encode_gpu", "ann_reorder_graph"]
 
 
 class AnnError(RuntimeError):
@@ -37,7 +38,8 @@ class GraphDesc(ctypes.Structure):
                 ("R", ctypes.c_int32), ("entry", ctypes.c_int32), ("vectors", ctypes.c_void_p),
                 ("adj", ctypes.c_void_p), ("M", ctypes.c_int32), ("codebook", ctypes.c_void_p),
                 ("codes", ctypes.c_void_p), ("tier", ctypes.c_int32), ("nav", ctypes.c_int32),
-                ("nav_scale", ctypes.c_float), ("rerank_mult", ctypes.c_int32)]
+                ("nav_scale", ctypes.c_float), ("rerank_mult", ctypes.c_int32),
+                ("id_map", ctypes.c_void_p)]
 
 
 class Trace(ctypes.Structure):
@@ -112,6 +114,9 @@ def lib():
                                  ctypes.POINTER(SearchStats)]
         L.ann_search_dev.restype = ctypes.c_int
         L.ann_search_dev.argtypes = [P, P, I64, I32, I32, I32, P, P, ctypes.POINTER(Trace), P]
+        L.ann_search_dev_kernel_grained.restype = ctypes.c_int
+        L.ann_search_dev_kernel_grained.argtypes = [P, P, I64, I32, I32, I32, P, P,
+                                                    ctypes.POINTER(Trace), P]
         L.ann_search_dev_noalloc.restype = ctypes.c_int
         L.ann_search_dev_noalloc.argtypes = [P, P, I64, I32, I32, I32, P, P,
                                              ctypes.POINTER(Trace), P]
@@ -129,6 +134,8 @@ def lib():
         L.ann_encode_bf16.argtypes = [P, I64, P]
         L.ann_encode_fp8e4m3.restype = ctypes.c_int
         L.ann_encode_fp8e4m3.argtypes = [P, I64, ctypes.c_float, P]
+        L.ann_reorder_graph.restype = ctypes.c_int
+        L.ann_reorder_graph.argtypes = [P, I32, I64, I32, I32, P, I32, P, I32, P, P, P, P, P]
         L.ann_pq_encode_gpu.restype = ctypes.c_int
         L.ann_pq_encode_gpu.argtypes = [P, I32, I64, I32, I32, P, P]
         L.ann_knn_exact.restype = ctypes.c_int

@@ -51,6 +51,8 @@ struct SearchArgs {
   const void* vectors;      // exact modes: n*d elements (HBM)
   const int32_t* adj;       // exact modes: n*adj_stride ids (HBM)
   int32_t adj_stride;       // ids per adjacency row (multiple of 4)
+  const int32_t* id_map;    // caller's id of each stored node, written to the results (HBM), or null
+  unsigned* grid_bar;       // kernel-grained I/O ablation: grid barrier state (4 words), or null
   // batch
   const void* queries;
   int32_t nq, k, L, depth;
@@ -141,12 +143,16 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
 cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
                         int64_t nq, SearchPlan* plan);
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream);
+// The same kernel as a cooperative launch (every block resident), for the
+// kernel-grained I/O ablation (a.grid_bar set).
+cudaError_t launch_search_coop(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream);
 // Persistent serving kernel (a.L / a.k are the largest L / k it accepts).
 cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,
                          cudaStream_t stream);
 
 // Exact FP32 rerank of kc candidates per query down to k (kc <= 256).
 cudaError_t launch_rerank(const float* vectors, int d, const float* queries, int nq, const int32_t* cand,
+                          const int32_t* id_map,
                           int kc, int k, int32_t* ids, float* dists, cudaStream_t st);
 
 // Storage-tier read probe kernel launcher.

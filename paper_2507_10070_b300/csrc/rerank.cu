@@ -12,8 +12,8 @@ namespace {
 constexpr int kRerankMax = 256;
 
 __global__ void rerank_kernel(const float* __restrict__ vectors, int d, const float* __restrict__ queries,
-                              int nq, const int32_t* __restrict__ cand, int kc, int k,
-                              int32_t* __restrict__ ids, float* __restrict__ dists) {
+                              int nq, const int32_t* __restrict__ cand, const int32_t* __restrict__ id_map,
+                              int kc, int k, int32_t* __restrict__ ids, float* __restrict__ dists) {
   __shared__ unsigned long long keys[4][kRerankMax];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int qi = blockIdx.x * 4 + wib;
@@ -60,7 +60,8 @@ __global__ void rerank_kernel(const float* __restrict__ vectors, int d, const fl
   for (int j = lane; j < k; j += 32) {
     const unsigned long long key = K[j];
     const bool ok = key != ~0ull;
-    ids[static_cast<size_t>(qi) * k + j] = ok ? static_cast<int32_t>(key & 0xffffffffu) : -1;
+    const int32_t id = static_cast<int32_t>(key & 0xffffffffu);
+    ids[static_cast<size_t>(qi) * k + j] = ok ? (id_map ? __ldg(id_map + id) : id) : -1;
     dists[static_cast<size_t>(qi) * k + j] =
         ok ? __uint_as_float(static_cast<unsigned>(key >> 32)) : __int_as_float(0x7f800000);
   }
@@ -69,10 +70,11 @@ __global__ void rerank_kernel(const float* __restrict__ vectors, int d, const fl
 }  // namespace
 
 cudaError_t launch_rerank(const float* vectors, int d, const float* queries, int nq, const int32_t* cand,
-                          int kc, int k, int32_t* ids, float* dists, cudaStream_t st) {
+                          const int32_t* id_map, int kc, int k, int32_t* ids, float* dists,
+                          cudaStream_t st) {
   if (kc > kRerankMax || k > kc) return cudaErrorInvalidValue;
   if (nq == 0) return cudaSuccess;
-  rerank_kernel<<<(nq + 3) / 4, 128, 0, st>>>(vectors, d, queries, nq, cand, kc, k, ids, dists);
+  rerank_kernel<<<(nq + 3) / 4, 128, 0, st>>>(vectors, d, queries, nq, cand, id_map, kc, k, ids, dists);
   return cudaGetLastError();
 }
 

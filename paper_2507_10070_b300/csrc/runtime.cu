@@ -78,8 +78,10 @@ struct ann_index {
   float nav_inv_scale = 1.f;
   int rerank_mult = 4;
   DevBuf rr_ids, rr_d;       // candidates before the exact rerank
+  DevBuf grid_bar;           // kernel-grained I/O ablation: grid barrier state
   void* vectors = nullptr;
   int32_t* adj = nullptr;
+  int32_t* id_map = nullptr;  // caller's id of each stored node (HBM), or null
   // scratch
   uint32_t* vis = nullptr;
   size_t vis_words = 0;
@@ -122,8 +124,10 @@ void release(ann_index* ix) {
   cudaFree(ix->nav);
   ix->rr_ids.release();
   ix->rr_d.release();
+  ix->grid_bar.release();
   cudaFree(ix->vectors);
   cudaFree(ix->adj);
+  cudaFree(ix->id_map);
   cudaFree(ix->vis);
   cudaFree(ix->counters);
   cudaFree(ix->expansions);
@@ -241,6 +245,10 @@ int ann_load_graph(ann_index** out, const ann_graph_desc* g) {
     const int32_t init[4] = {0, 0, INT32_MAX, 0};
     ANN_TRY(cudaMemcpy(ix->counters, init, sizeof(init), cudaMemcpyHostToDevice), "upload counters");
     ANN_TRY(cudaMemset(ix->expansions, 0, sizeof(unsigned long long)), "cudaMemset");
+  }
+  if (g->id_map) {
+    ANN_TRY(cudaMalloc(&ix->id_map, (size_t)n * 4), "cudaMalloc id map");
+    ANN_TRY(cudaMemcpy(ix->id_map, g->id_map, (size_t)n * 4, cudaMemcpyHostToDevice), "upload id map");
   }
   if (ix->mode == kModePqU8) {
     // Node block: [vector d bytes][R int32 ids][uint32 degree][zero pad to 128 B]
@@ -362,7 +370,8 @@ int validate_search(const ann_index* ix, const void* q, int64_t nq, int k, int L
 bool rerank_mode(int mode) { return mode == kModeBF16 || mode == kModeFP8 || mode == kModePqF32; }
 
 int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int depth, int32_t* ids,
-                   float* dists, const ann_trace* tr, cudaStream_t st, bool timed) {
+                   float* dists, const ann_trace* tr, cudaStream_t st, bool timed,
+                   bool kernel_grained = false) {
   if (nq == 0) return ANN_OK;
   const int slot_bytes = ix->slot_bytes;
   // precision variants: keep the top rerank_mult*k expanded by navigation
@@ -423,6 +432,16 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   a.vectors = ix->vectors;
   a.adj = ix->adj;
   a.adj_stride = ix->adj_stride;
+  a.id_map = rr ? nullptr : ix->id_map;  // with a rerank, the rerank maps the final ids
+  a.grid_bar = nullptr;
+  if (kernel_grained) {
+    e = ix->grid_bar.ensure(4 * sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_error(e, "grid barrier state");
+    const unsigned init[4] = {0u, 0u, static_cast<unsigned>(plan.blocks * plan.warps_per_block), 0u};
+    e = cudaMemcpyAsync(ix->grid_bar.p, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "grid barrier state");
+    a.grid_bar = static_cast<unsigned*>(ix->grid_bar.p);
+  }
   a.queries = q;
   a.nq = (int32_t)nq;
   a.k = k;
@@ -443,11 +462,11 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   e = cudaMemsetAsync(ix->counters, 0, sizeof(int32_t), st);  // next-query counter
   if (e != cudaSuccess) return cuda_error(e, "reset work counter");
   if (timed) cudaEventRecord(ix->ev0, st);
-  e = launch_search(a, plan, st);
+  e = kernel_grained ? launch_search_coop(a, plan, st) : launch_search(a, plan, st);
   if (e != cudaSuccess) return cuda_error(e, "search kernel launch");
   if (rr) {
     e = launch_rerank(static_cast<const float*>(ix->vectors), ix->d, static_cast<const float*>(q), (int)nq,
-                      ids, k, k_out, ids_out, dists_out, st);
+                      ids, ix->id_map, k, k_out, ids_out, dists_out, st);
     if (e != cudaSuccess) return cuda_error(e, "rerank kernel launch");
   }
   if (timed) cudaEventRecord(ix->ev1, st);
@@ -477,6 +496,8 @@ int collect(ann_index* ix, cudaStream_t st, int64_t queries, ann_search_stats* s
     stats->first_failed = c[1] > 0 ? c[2] : -1;
     stats->kernel_ms = ms;
   }
+  if (c[3] != 0)
+    return set_error(ANN_ETIMEOUT, "a kernel-grained round barrier timed out (%d queries failed)", c[1]);
   if (c[1] > 0)
     return set_error(ANN_ENOMEM, "%d queries overflowed their visited set (first: query %d)", c[1], c[2]);
   return ANN_OK;
@@ -554,6 +575,21 @@ int ann_search_dev(ann_index* ix, const void* queries, int64_t nq, int32_t k, in
   if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
   rc = enqueue_search(ix, queries, nq, k, L, depth, ids, dists, trace,
                       static_cast<cudaStream_t>(stream), false);
+  if (rc == ANN_OK) ix->pending_queries += nq;
+  return rc;
+}
+
+int ann_search_dev_kernel_grained(ann_index* ix, const void* queries, int64_t nq, int32_t k, int32_t L,
+                                  int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
+                                  void* stream) {
+  int rc = validate_search(ix, queries, nq, k, L, depth, ids, dists);
+  if (rc != ANN_OK) return rc;
+  if (reinterpret_cast<uintptr_t>(queries) % 16)
+    return set_error(ANN_EINVAL, "queries must be 16-byte aligned");
+  BusyGuard guard(ix);
+  if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
+  rc = enqueue_search(ix, queries, nq, k, L, depth, ids, dists, trace,
+                      static_cast<cudaStream_t>(stream), false, true);
   if (rc == ANN_OK) ix->pending_queries += nq;
   return rc;
 }
@@ -640,7 +676,7 @@ namespace {
 struct FileHeader {
   char magic[8];
   int64_t n;
-  int32_t d, dtype, R, entry, M, zero;
+  int32_t d, dtype, R, entry, M, flags;  // flags: bit 0 = an id map follows the codes
 };
 
 bool write_all(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
@@ -666,13 +702,14 @@ int ann_save_graph_file(const char* path, const ann_graph_desc* g) {
   h.R = g->R;
   h.entry = g->entry;
   h.M = g->M;
-  h.zero = 0;
+  h.flags = g->id_map ? 1 : 0;
   bool ok = write_all(f, &h, sizeof(h)) &&
             write_all(f, g->vectors, (size_t)g->n * g->d * elt_size(g->dtype)) &&
             write_all(f, g->adj, (size_t)g->n * g->R * 4);
   if (ok && g->M > 0)
     ok = write_all(f, g->codebook, (size_t)g->M * 256 * (g->d / g->M) * 4) &&
          write_all(f, g->codes, (size_t)g->n * g->M);
+  if (ok && g->id_map) ok = write_all(f, g->id_map, (size_t)g->n * 4);
   ok = (fclose(f) == 0) && ok;
   return ok ? ANN_OK : set_error(ANN_EIO, "short write to %s", path);
 }
@@ -688,7 +725,8 @@ int ann_load_graph_file(ann_index** out, const char* path, int32_t tier) {
     return set_error(ANN_EIO, "%s is not an index file", path);
   }
   if (h.n < 1 || h.n >= INT32_MAX || h.d < 4 || h.d > kMaxD || h.R < 1 || h.R > kMaxR ||
-      h.M < 0 || h.M > kMaxM || (h.M > 0 && h.d % h.M) || (h.dtype != ANN_U8 && h.dtype != ANN_F32)) {
+      h.M < 0 || h.M > kMaxM || (h.M > 0 && h.d % h.M) || (h.dtype != ANN_U8 && h.dtype != ANN_F32) ||
+      (h.flags & ~1)) {
     fclose(f);
     return set_error(ANN_EIO, "%s: corrupt header", path);
   }
@@ -702,9 +740,14 @@ int ann_load_graph_file(ann_index** out, const char* path, int32_t tier) {
     codes.resize((size_t)h.n * h.M);
     ok = read_all(f, cb.data(), cb.size() * 4) && read_all(f, codes.data(), codes.size());
   }
+  std::vector<int32_t> id_map;
+  if (ok && (h.flags & 1)) {
+    id_map.resize((size_t)h.n);
+    ok = read_all(f, id_map.data(), id_map.size() * 4);
+  }
   fclose(f);
   if (!ok) return set_error(ANN_EIO, "%s is truncated", path);
-  ann_graph_desc g;
+  ann_graph_desc g{};
   g.n = h.n;
   g.d = h.d;
   g.dtype = h.dtype;
@@ -716,6 +759,7 @@ int ann_load_graph_file(ann_index** out, const char* path, int32_t tier) {
   g.codebook = h.M > 0 ? cb.data() : nullptr;
   g.codes = h.M > 0 ? codes.data() : nullptr;
   g.tier = tier;
+  g.id_map = id_map.empty() ? nullptr : id_map.data();
   return ann_load_graph(out, &g);
 }
 
@@ -749,6 +793,7 @@ int index_search_view(const ann_index* ix, SearchArgs* a, int* mode, int* slot_b
   a->vectors = ix->vectors;
   a->adj = ix->adj;
   a->adj_stride = ix->adj_stride;
+  a->id_map = ix->id_map;
   *mode = ix->mode;
   *slot_bytes = ix->slot_bytes;
   return ANN_OK;

@@ -146,6 +146,56 @@ __device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int 
   return lo;
 }
 
+// ---- Kernel-grained I/O, the ablation of the query-grained I/O stack
+// (Section "Resource-Efficient Query-Grained Concurrent I/O Stack" compares
+// against CAM, where the kernel waits for every request of the batch): with
+// a.grid_bar set, every resident warp meets at a grid-wide barrier after
+// each fetch wait, so no query expands a node before the fetches of all
+// warps in that round have arrived.  bar: [0] arrivals, [1] generation,
+// [2] warps still searching, [3] 1 once every warp has stopped searching
+// (written by the last arrival of a round).  Needs a cooperative launch
+// (all blocks resident).  Waits are bounded: past the limit the warp sets
+// counters[3] and gives up, and every other waiting warp gives up with it.
+constexpr unsigned kRoundSpinLimit = 1u << 22;  // x >= 100 ns sleeps: ~0.5 s or more
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One barrier round for the calling warp.  Returns false if the wait ran
+// out; *all_done = every warp had stopped searching when the round closed.
+__device__ bool grid_round(unsigned* bar, int* timed_out, int lane, int* all_done) {
+  const unsigned total = gridDim.x * (blockDim.x >> 5);
+  int ok = 1, fin = 0;
+  if (lane == 0) {
+    const unsigned gen = ld_acquire_gpu_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == total - 1) {
+      // every other warp is waiting here, so the searching count is final
+      fin = atomicAdd(bar + 2, 0u) == 0u;
+      bar[3] = static_cast<unsigned>(fin);
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire_gpu_u32(bar + 1) == gen) {
+        if (++spins > kRoundSpinLimit || ld_acquire_gpu_u32(reinterpret_cast<unsigned*>(timed_out))) {
+          atomicExch(timed_out, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+      if (ok) fin = static_cast<int>(ld_acquire_gpu_u32(bar + 3));
+    }
+  }
+  *all_done = __shfl_sync(kFull, fin, 0);
+  return __shfl_sync(kFull, ok, 0) != 0;
+}
+
 __device__ __forceinline__ unsigned hash_slot(unsigned id, int log2cap) {
   return (id * 2654435761u) >> (32 - log2cap);
 }
@@ -466,6 +516,13 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       // ---- a5: wait for this warp's oldest fetch only
       cp_async_wait_pending(inflight - 1);
       __syncwarp();
+      if (a.grid_bar) {  // kernel-grained ablation: the round's fetches all land first
+        int all_done;
+        if (!grid_round(a.grid_bar, a.counters + 3, lane, &all_done)) {
+          status = ANN_ETIMEOUT;
+          break;
+        }
+      }
       const unsigned char* blk = ring + head * slot_bytes;
       const unsigned long long ukey = ring_key[head];
       const unsigned u = static_cast<unsigned>(ukey);
@@ -701,7 +758,8 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   for (int j = lane; j < k; j += 32) {
     const unsigned long long r = j < s.nres ? res[j] : kNoKey;
     const bool ok = r != kNoKey;
-    job.ids[j] = ok ? static_cast<int32_t>(r & 0xffffffffu) : -1;
+    const int32_t id = static_cast<int32_t>(r & 0xffffffffu);
+    job.ids[j] = ok ? (a.id_map ? __ldg(a.id_map + id) : id) : -1;
     const unsigned dbits = static_cast<unsigned>(r >> 32);
     job.dists[j] = ok ? (mode_f32(MODE) ? __uint_as_float(dbits) : static_cast<float>(dbits))
                       : __int_as_float(0x7f800000);
@@ -736,6 +794,7 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
   uint32_t* vis = a.vis + (gw << a.vis_log2);
   uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
   for (;;) {
+    if (a.grid_bar && ld_acquire_gpu_u32(reinterpret_cast<const unsigned*>(a.counters + 3))) break;
     int qi = 0;
     if (lane == 0) qi = atomicAdd(&a.counters[0], 1);
     qi = __shfl_sync(kFull, qi, 0);
@@ -753,6 +812,19 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
     job.t_begin = a.t_begin ? a.t_begin + qi : nullptr;
     job.t_end = a.t_end ? a.t_end + qi : nullptr;
     run_query<MODE, NB>(a, job, ws, lay, vis, vlog, lane);
+  }
+  if (a.grid_bar) {
+    // kernel-grained ablation: stop searching, but keep meeting the other
+    // warps' rounds until every warp has stopped
+    if (lane == 0) {
+      __threadfence();
+      atomicSub(a.grid_bar + 2, 1u);
+    }
+    __syncwarp();
+    for (;;) {
+      int all_done = 0;
+      if (!grid_round(a.grid_bar, a.counters + 3, lane, &all_done) || all_done) break;
+    }
   }
 }
 
@@ -891,6 +963,20 @@ cudaError_t launch_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) 
 }
 
 template <int MODE, int NB>
+cudaError_t launch_coop_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) {
+  const int smem = p.smem_per_warp * p.warps_per_block;
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  SearchArgs args = a;
+  int spw = p.smem_per_warp;
+  void* params[] = {&args, &spw};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(search_kernel<MODE, NB>),
+                                     dim3(p.blocks), dim3(32 * p.warps_per_block), params,
+                                     static_cast<size_t>(smem), st);
+}
+
+template <int MODE, int NB>
 cudaError_t occupancy_t(int smem_block, int threads, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block);
@@ -964,6 +1050,17 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
 
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
   return launch_table(plan.mode, plan.nb)(a, plan, stream);
+}
+
+cudaError_t launch_search_coop(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
+  static const LaunchFn t[kNumModes][3] = {
+      {launch_coop_t<kModePqU8, 1>, launch_coop_t<kModePqU8, 2>, launch_coop_t<kModePqU8, 4>},
+      {launch_coop_t<kModeExactU8, 1>, launch_coop_t<kModeExactU8, 2>, launch_coop_t<kModeExactU8, 4>},
+      {launch_coop_t<kModeExactF32, 1>, launch_coop_t<kModeExactF32, 2>, launch_coop_t<kModeExactF32, 4>},
+      {launch_coop_t<kModeBF16, 1>, launch_coop_t<kModeBF16, 2>, launch_coop_t<kModeBF16, 4>},
+      {launch_coop_t<kModeFP8, 1>, launch_coop_t<kModeFP8, 2>, launch_coop_t<kModeFP8, 4>},
+      {launch_coop_t<kModePqF32, 1>, launch_coop_t<kModePqF32, 2>, launch_coop_t<kModePqF32, 4>}};
+  return t[plan.mode][nb_index(plan.nb)](a, plan, stream);
 }
 
 cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& s, const SearchPlan& plan,

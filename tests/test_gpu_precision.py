@@ -70,6 +70,22 @@ def test_precision_variant_matches_oracle(deep, variant, depth):
     assert np.all(np.abs(d - d64)[ids >= 0] <= 1e-5 * d64[ids >= 0] + 1e-7)
 
 
+def test_rerank_reports_mapped_ids(deep):
+    n = deep["base"].shape[0]
+    labels = (np.arange(n) * 5 + 1).astype(np.int32)
+    a = ann.Index(deep["base"], deep["adj"], deep["entry"], tier=ann.ANN_TIER_HBM, nav=ann.ANN_NAV_BF16)
+    b = ann.Index(deep["base"], deep["adj"], deep["entry"], tier=ann.ANN_TIER_HBM, nav=ann.ANN_NAV_BF16,
+                  id_map=labels)
+    try:
+        ai, ad, _ = a.search(deep["q"], 10, 64, 1)
+        bi, bd, _ = b.search(deep["q"], 10, 64, 1)
+    finally:
+        a.close()
+        b.close()
+    assert np.array_equal(bi, np.where(ai >= 0, labels[np.maximum(ai, 0)], -1))
+    assert np.array_equal(bd, ad)
+
+
 def test_fp32_navigation_is_the_reference(deep):
     """The FP32 traversal (exact navigation) that the variants are compared with."""
     w = deep

@@ -207,6 +207,87 @@ def test_repeated_ids_and_self_links(u8_pq, L, depth):
     assert np.array_equal(tr["steps"], os_)
 
 
+def _relabel(ids, labels):
+    return np.where(ids >= 0, labels[np.maximum(ids, 0)], -1)
+
+
+def test_id_map_relabels_results(u8_pq, pq_index, tmp_path):
+    """An index loaded with an id map reports id_map[node] and searches as
+    before: batch call, index file, exact-navigation index."""
+    w = u8_pq
+    n = w["base"].shape[0]
+    labels = (np.arange(n, dtype=np.int64) * 3 + 11).astype(np.int32)
+    ref_i, ref_d, _ = pq_index.search(w["q"], 10, 64, 1)
+    ixm = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],
+                    tier=ann.ANN_TIER_HOST_PINNED, id_map=labels)
+    try:
+        i1, d1, _ = ixm.search(w["q"], 10, 64, 1)
+    finally:
+        ixm.close()
+    assert np.array_equal(i1, _relabel(ref_i, labels)) and np.array_equal(d1, ref_d)
+    path = str(tmp_path / "mapped.idx")
+    ann.save_index(path, w["base"], w["adj"], w["entry"], w["cb"], w["codes"], id_map=labels)
+    ixf = ann.Index(path=path, tier=ann.ANN_TIER_HOST_PINNED)
+    try:
+        i2, d2, _ = ixf.search(w["q"], 10, 64, 1)
+    finally:
+        ixf.close()
+    assert np.array_equal(i2, i1) and np.array_equal(d2, ref_d)
+    e0 = ann.Index(w["base"], w["adj"], w["entry"], tier=ann.ANN_TIER_HBM)
+    e1 = ann.Index(w["base"], w["adj"], w["entry"], tier=ann.ANN_TIER_HBM, id_map=labels)
+    try:
+        a_i, a_d, _ = e0.search(w["q"], 10, 32, 2)
+        b_i, b_d, _ = e1.search(w["q"], 10, 32, 2)
+    finally:
+        e0.close()
+        e1.close()
+    assert np.array_equal(b_i, _relabel(a_i, labels)) and np.array_equal(b_d, a_d)
+
+
+@pytest.mark.parametrize("L,depth", [(64, 1), (256, 0)])
+def test_breadth_first_layout_matches_oracle(u8_pq, L, depth):
+    """The kernel on the breadth-first reordered index reports original ids
+    (through the id map) and equals the oracle searching the same reordered
+    index, mapped back the same way."""
+    w = u8_pq
+    b2, a2, e2, c2, old = ann.reorder_graph(w["base"], w["adj"], w["entry"], w["codes"])
+    ix = ann.Index(b2, a2, e2, w["cb"], c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
+    try:
+        ids, d, _, tr = ix.search(w["q"], 10, L, depth, trace=True)
+    finally:
+        ix.close()
+    oi, od, os_ = oracle.search(b2, a2, e2, w["q"], 10, L, depth, codebook=w["cb"], codes=c2)
+    assert np.array_equal(ids, _relabel(oi, old)) and np.array_equal(d.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
+@pytest.mark.parametrize("depth", [0, 1])
+def test_kernel_grained_ablation_matches_query_grained(u8_pq, pq_index, depth):
+    """The kernel-grained I/O ablation (grid barrier after every fetch wait)
+    changes only timing: results and step counts equal the query-grained
+    search, for a full grid and for fewer queries than resident warps."""
+    import torch
+    w = u8_pq
+    st = torch.cuda.Stream()
+
+    def run(fn, qh):
+        q = torch.from_numpy(qh).cuda()
+        nq = q.shape[0]
+        ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
+        d = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+        steps = torch.empty(nq, dtype=torch.int32, device="cuda")
+        fn(q, 10, 64, depth, ids, d, stream=st, trace={"steps": steps})
+        stats = pq_index.sync(st)
+        return ids.cpu().numpy(), d.cpu().numpy(), steps.cpu().numpy(), stats
+
+    for qh in (w["q"], w["q"][:5]):
+        a = run(pq_index.search_dev, qh)
+        b = run(pq_index.search_dev_kernel_grained, qh)
+        assert b[3].n_failed == 0 and b[3].expansions == a[3].expansions
+        for x, y in zip(a[:3], b[:3]):
+            assert np.array_equal(x, y)
+
+
 def test_visited_overflow_reports_enomem():
     """The device's failure path, checked from the host: on a ring lattice
     (node i -> i+1..i+R, positions on a line) a query at the far end makes the

@@ -106,6 +106,23 @@ def test_idle_exit_and_relaunch(served):
         srv.close()
 
 
+def test_served_results_carry_the_id_map(served):
+    ix, q = served["ix"], served["q"]
+    n = served["base"].shape[0]
+    labels = (n - 1 - np.arange(n)).astype(np.int32)
+    ixm = ann.Index(served["base"], served["adj"], served["entry"], served["cb"], served["codes"],
+                    tier=ann.ANN_TIER_HOST_PINNED, id_map=labels)
+    srv = ann.Server(ixm, max_L=128, max_k=10, depth=1, slots=256)
+    try:
+        got_i, got_d, _ = srv.poll(srv.submit(q[:64], 10, 96), 10_000_000)
+    finally:
+        srv.close()
+        ixm.close()
+    ref_i, ref_d, _ = ix.search(q[:64], 10, 96, 1)
+    assert np.array_equal(got_i, np.where(ref_i >= 0, labels[np.maximum(ref_i, 0)], -1))
+    assert np.array_equal(got_d, ref_d)
+
+
 def test_concurrent_submitters(served):
     ix, q = served["ix"], served["q"]
     srv = ann.Server(ix, max_L=256, max_k=10, depth=2, slots=2048)

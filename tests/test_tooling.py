@@ -1,5 +1,6 @@
 """Index-construction tooling of the library (host threads) against the oracle."""
 import numpy as np
+import pytest
 
 import datagen
 import oracle
@@ -34,3 +35,87 @@ def test_build_graph_invariants_and_quality():
     gi, gd = oracle.knn(base, q, 10)
     ids, d, _ = oracle.search(base, adj, entry, q, 10, 64, 0)
     assert oracle.recall_at_k(ids, gi, gd, d) >= 0.95
+
+
+def _bfs(adj, entry):
+    """Breadth-first order written out: neighbours in row order up to the
+    first -1; when the queue runs dry, breadth-first again from the lowest
+    id not yet placed."""
+    import collections
+    n = adj.shape[0]
+    pos = np.full(n, -1)
+    order = [entry]
+    pos[entry] = 0
+    dq = collections.deque([entry])
+    nxt = 0
+    while len(order) < n:
+        if not dq:
+            while pos[nxt] >= 0:
+                nxt += 1
+            pos[nxt] = len(order)
+            order.append(nxt)
+            dq.append(nxt)
+        u = dq.popleft()
+        for w in adj[u]:
+            if w < 0:
+                break
+            if pos[w] < 0:
+                pos[w] = len(order)
+                order.append(w)
+                dq.append(w)
+    return np.array(order)
+
+
+def test_reorder_graph_is_breadth_first_and_relabels():
+    rng = np.random.default_rng(3)
+    n, R = 3000, 12
+    adj = rng.integers(0, n, (n, R)).astype(np.int32)          # repeats and self links
+    adj[rng.random((n, R)) < 0.2] = -1                          # rows end at the first -1
+    adj[:50] = -1                                               # nodes 0..49 have no out-edges
+    adj[:, :1][adj[:, :1] < 50] = 100                           # ... and nobody links to them
+    adj[(adj >= 0) & (adj < 50)] = 200
+    base = rng.integers(0, 256, (n, 16)).astype(np.uint8)
+    codes = rng.integers(0, 256, (n, 4)).astype(np.uint8)
+    b2, a2, e2, c2, old = ann.reorder_graph(base, adj, 777, codes)
+    assert np.array_equal(old, _bfs(adj, 777)) and e2 == 0
+    pos = np.empty(n, np.int64)
+    pos[old] = np.arange(n)
+    assert np.all(np.diff(pos[:50]) > 0) and pos[0] > n // 2     # isolated nodes: late, in id order
+    assert np.array_equal(b2, base[old]) and np.array_equal(c2, codes[old])
+    assert np.array_equal(a2, np.where(adj[old] >= 0, pos[np.maximum(adj[old], 0)], -1))
+    with pytest.raises(ann.AnnError):
+        bad = adj.copy()
+        bad[5, 0] = n
+        ann.reorder_graph(base, bad, 0, codes)
+
+
+def test_reordered_index_searches_the_same_graph():
+    """The oracle on the reordered index, with ids mapped back, equals the
+    oracle on the original (float32 data: no distance ties)."""
+    mx = datagen.inmemory_f32()
+    base, q = mx.base(4000), mx.queries(100)
+    entry = oracle.medoid(base)
+    adj = oracle.vamana(base, 32, 1.2, 64, entry, datagen.build_order(mx.seed, 4000),
+                        datagen.random_out_neighbours(mx.seed, 4000, 32))
+    b2, a2, e2, _, old = ann.reorder_graph(base, adj, entry)
+    for depth in (0, 2):
+        i0, d0, s0 = oracle.search(base, adj, entry, q, 10, 48, depth)
+        i1, d1, s1 = oracle.search(b2, a2, e2, q, 10, 48, depth)
+        assert np.array_equal(old[i1], i0) and np.array_equal(d1, d0) and np.array_equal(s1, s0)
+
+
+def test_index_file_keeps_the_id_map(tmp_path):
+    rng = np.random.default_rng(1)
+    n = 500
+    base = rng.integers(0, 256, (n, 64)).astype(np.uint8)
+    adj = rng.integers(0, n, (n, 8)).astype(np.int32)
+    cb = rng.integers(0, 256, (16, 256, 4)).astype(np.float32)
+    codes = rng.integers(0, 256, (n, 16)).astype(np.uint8)
+    labels = (np.arange(n) * 7 + 3).astype(np.int32)
+    p0, p1 = str(tmp_path / "a.idx"), str(tmp_path / "b.idx")
+    ann.save_index(p0, base, adj, 0, cb, codes)
+    ann.save_index(p1, base, adj, 0, cb, codes, id_map=labels)
+    h0, h1 = open(p0, "rb").read(), open(p1, "rb").read()
+    assert len(h1) == len(h0) + 4 * n
+    assert np.frombuffer(h0[36:40], np.int32)[0] == 0 and np.frombuffer(h1[36:40], np.int32)[0] == 1
+    assert np.array_equal(np.frombuffer(h1[-4 * n:], np.int32), labels)

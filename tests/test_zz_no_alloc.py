@@ -92,3 +92,28 @@ def test_noalloc_reports_status_and_rejects_oversized_scratch(small_index):
         torch.cuda.synchronize()
     finally:
         wide.close()
+
+
+def test_noalloc_reports_mapped_ids(small_index):
+    import torch
+    ix, qh = small_index
+    mx = datagen.sift_like()
+    base = mx.base(20_000)
+    n = base.shape[0]
+    labels = (np.arange(n) * 2 + 9).astype(np.int32)
+    cb, codes = ann.build_pq(base, 32, n_train=5000, iters=5,
+                             kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, 32))
+    adj, entry = ann.build_graph(base, 64, 1.2, 64, seed=mx.seed)
+    ixm = ann.Index(base, adj, entry, cb, codes, tier=ann.ANN_TIER_HOST_PINNED, id_map=labels)
+    try:
+        q = torch.from_numpy(qh[:200]).cuda()
+        st = torch.cuda.Stream()
+        ids = torch.empty((200, 10), dtype=torch.int32, device="cuda")
+        d = torch.empty((200, 10), dtype=torch.float32, device="cuda")
+        ixm.search_dev_noalloc(q, 10, 128, 1, ids, d, stream=st)
+        st.synchronize()
+    finally:
+        ixm.close()
+    ref_i, ref_d, _ = ix.search(qh[:200], 10, 128, 1)
+    assert np.array_equal(ids.cpu().numpy(), np.where(ref_i >= 0, labels[np.maximum(ref_i, 0)], -1))
+    assert np.array_equal(d.cpu().numpy(), ref_d)
