@@ -415,17 +415,35 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   }
   __syncwarp();
 
-  // ---- a1: lookup table T[m][c], exact integers
+  // ---- a1: lookup table T[m][c], exact integers.  The codebook comes from
+  // L2 (shared memory leaves little L1), so each lane keeps two subspaces'
+  // eight centroids (16 loads) in flight instead of paying the latency once
+  // per entry; M is a multiple of 16.
   if (MODE == kModePqU8) {
     const int wps = a.dsub >> 2;  // 32-bit words per subvector
     const unsigned* qw = reinterpret_cast<const unsigned*>(qs);
-    for (int m = 0; m < a.M; ++m) {
-      for (int c = lane; c < 256; c += 32) {
-        const unsigned* cw = a.cb_words + (static_cast<size_t>(m) * 256 + c) * wps;
-        unsigned acc = 0;
-        for (int w = 0; w < wps; ++w) acc = sq4(qw[m * wps + w], __ldg(cw + w), acc);
-        lut[m * 256 + c] = acc;
+    for (int m = 0; m < a.M; m += 2) {
+      unsigned acc[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[h][j] = 0u;
+      for (int w = 0; w < wps; ++w) {
+        unsigned cv[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            cv[h][j] = __ldg(a.cb_words + (static_cast<size_t>(m + h) * 256 + lane + 32 * j) * wps + w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[h][j] = sq4(qw[(m + h) * wps + w], cv[h][j], acc[h][j]);
       }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) lut[(m + h) * 256 + lane + 32 * j] = acc[h][j];
     }
     __syncwarp();
   }
@@ -435,15 +453,24 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
     const float* qf = reinterpret_cast<const float*>(qs);
     const int dsub = a.dsub;
     for (int m = 0; m < a.M; ++m) {
-      for (int c = lane; c < 256; c += 32) {
-        const float* cc = a.cb_f32 + (static_cast<size_t>(m) * 256 + c) * dsub;
-        float acc = 0.f;
-        for (int j = 0; j < dsub; ++j) {
-          const float t = qf[m * dsub + j] - __ldg(cc + j);
-          acc = fmaf(t, t, acc);
+      // eight centroids per lane in flight; each sums its coordinates in order
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+      for (int j = 0; j < dsub; ++j) {
+        float cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          cv[u] = __ldg(a.cb_f32 + (static_cast<size_t>(m) * 256 + lane + 32 * u) * dsub + j);
+        const float qv = qf[m * dsub + j];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float t = qv - cv[u];
+          acc[u] = fmaf(t, t, acc[u]);
         }
-        lutf[m * 256 + c] = acc;
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lutf[m * 256 + lane + 32 * u] = acc[u];
     }
     __syncwarp();
   }
@@ -767,7 +794,18 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   // Clear the slots this query used, so the table is all zero for the next
   // query of this warp.
   __syncwarp();
-  for (int j = lane; j < visited; j += 32) vis[vlog[j]] = 0u;
+  // (eight log entries per lane in flight: the log is read back from L2)
+  for (int j0 = 0; j0 < visited; j0 += 256) {
+    unsigned slot[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 32 * u + lane;
+      slot[u] = j < visited ? vlog[j] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (slot[u] != 0xffffffffu) vis[slot[u]] = 0u;
+  }
   if (lane == 0) {
     if (job.steps) *job.steps = steps;
     if (job.status) *job.status = status;
