@@ -326,7 +326,8 @@ def run_ours(args, rank: int, world: int):
                      "dram_traffic": int(NCU_DRAM_BYTES_PER_EXPANSION * st.expansions / args.steps),
                      "peak_source": f"measured in-run: random {fetch_bytes} B reads of host pinned memory (the search's per-expansion fetch) by a full-occupancy probe kernel (ann_probe_read_bandwidth)",
                      "algorithmic_bytes_per_launch": int(bytes_per_launch),
-                     "hbm_peak_gbs": measured_peaks().get("hbm_gbs")},
+                     "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6400.0),
+                     "hbm_peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in measured_peaks() else "fallback (6.4 TB/s, one earlier B300 measurement)"},
         "setup_s": round(setup_s, 1),
         "index": {"builder": args.builder, "seconds_incl_pq_and_data": round(index_build_s, 1)},
     }
@@ -634,6 +635,17 @@ def run_large(args):
     out["hbm_tier_context"] = {"what": "the same index with its node blocks in HBM instead of host memory",
                                "by_depth": {str(d): v for d, v in sweep(ixh, (0, 1)).items()}}
     ixh.close()
+    # graph quality apart from PQ: the same graph navigated on exact distances
+    ixe = ann.Index(b2, a2, e2, tier=ann.ANN_TIER_HBM, id_map=old)
+    exact = {}
+    for Lx in (L, 2 * L):
+        ixe.search_dev(qd, k, Lx, 0, ids, dists, stream=stream)
+        ixe.sync(stream)
+        exact[str(Lx)] = round(ann.recall_at_k(ids.cpu().numpy(), gt_ids, gt_d, dists.cpu().numpy()), 4)
+    ixe.close()
+    out["exact_navigation_recall_at_10"] = {
+        "what": "recall@10 of the same graph navigated on exact distances (vectors in HBM), depth 0: graph quality without PQ noise",
+        "by_L": exact}
     if not args.no_cpu_baseline:
         w = {"base": b2, "adj": a2, "entry": e2, "cb": cb, "codes": c2, "q": q}
         out["cpu_baseline"] = cpu_baseline(w, L, 1000)
