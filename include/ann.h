@@ -193,8 +193,10 @@ int ann_search_dev(ann_index* index, const void* queries, int64_t nq, int32_t k,
  * barrier after each fetch wait: no query expands a node until the fetches
  * of every resident warp in that round have arrived.  The barrier's waits
  * are bounded; if one runs out, the queries still running report
- * ANN_ETIMEOUT and the next ann_sync returns ANN_ETIMEOUT.  For measurement
- * only -- query-grained I/O (ann_search_dev) is never slower.
+ * ANN_ETIMEOUT, the queries not started yet are left unwritten, and the
+ * next ann_sync returns ANN_ETIMEOUT; the index stays usable.  (Tests force
+ * this path with the environment variable ANN_TEST_STALL_ROUNDS=1.)  For
+ * measurement only -- query-grained I/O (ann_search_dev) is never slower.
  */
 int ann_search_dev_kernel_grained(ann_index* index, const void* queries, int64_t nq, int32_t k,
                                   int32_t L, int32_t depth, int32_t* ids, float* dists,

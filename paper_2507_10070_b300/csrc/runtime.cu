@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -437,7 +438,13 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   if (kernel_grained) {
     e = ix->grid_bar.ensure(4 * sizeof(unsigned));
     if (e != cudaSuccess) return cuda_error(e, "grid barrier state");
-    const unsigned init[4] = {0u, 0u, static_cast<unsigned>(plan.blocks * plan.warps_per_block), 0u};
+    const unsigned warps = static_cast<unsigned>(plan.blocks * plan.warps_per_block);
+    // Test hook for the bounded waits: ANN_TEST_STALL_ROUNDS=1 presets the
+    // arrival count past the last arrival, so no round can complete and
+    // every warp must give up (the call then reports ANN_ETIMEOUT).
+    const char* stall = std::getenv("ANN_TEST_STALL_ROUNDS");
+    const unsigned arrivals = (stall && stall[0] == '1') ? warps : 0u;
+    const unsigned init[4] = {arrivals, 0u, warps, 0u};
     e = cudaMemcpyAsync(ix->grid_bar.p, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_error(e, "grid barrier state");
     a.grid_bar = static_cast<unsigned*>(ix->grid_bar.p);

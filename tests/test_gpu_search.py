@@ -288,6 +288,29 @@ def test_kernel_grained_ablation_matches_query_grained(u8_pq, pq_index, depth):
             assert np.array_equal(x, y)
 
 
+def test_kernel_grained_bounded_wait_reports_timeout(u8_pq, pq_index, monkeypatch):
+    """The ablation's barrier waits are bounded.  A host-side hook presets its
+    arrival count so that no round can ever complete: every warp must give
+    up after its bounded spin, the call must report ANN_ETIMEOUT, and the
+    index must keep working afterwards."""
+    import torch
+    w = u8_pq
+    q = torch.from_numpy(w["q"][:64]).cuda()
+    ids = torch.empty((64, 10), dtype=torch.int32, device="cuda")
+    d = torch.empty((64, 10), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    monkeypatch.setenv("ANN_TEST_STALL_ROUNDS", "1")
+    pq_index.search_dev_kernel_grained(q, 10, 64, 0, ids, d, stream=st)
+    with pytest.raises(ann.AnnError) as e:
+        pq_index.sync(st)
+    assert e.value.status == ann._abi.ANN_ETIMEOUT
+    monkeypatch.delenv("ANN_TEST_STALL_ROUNDS")
+    pq_index.search_dev_kernel_grained(q, 10, 64, 0, ids, d, stream=st)
+    assert pq_index.sync(st).n_failed == 0
+    ref_i, ref_d, _ = pq_index.search(w["q"][:64], 10, 64, 0)
+    assert np.array_equal(ids.cpu().numpy(), ref_i) and np.array_equal(d.cpu().numpy(), ref_d)
+
+
 def test_visited_overflow_reports_enomem():
     """The device's failure path, checked from the host: on a ring lattice
     (node i -> i+1..i+R, positions on a line) a query at the far end makes the
