@@ -42,7 +42,7 @@ DATA = os.path.join(ROOT, "_data")
 # expansion (profiles/search_kernel_pq_sift200k_L256.md): PCIe read bytes
 # (the storage tier, which bounds the kernel) and DRAM read + write bytes.
 NCU_PCIE_BYTES_PER_EXPANSION = 420.0
-NCU_DRAM_BYTES_PER_EXPANSION = 508.0
+NCU_DRAM_BYTES_PER_EXPANSION = 513.0
 METRIC = "QPS at recall@10>=0.95 on 1 B300, relaxed vs sync search; p50/p99 latency"
 WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Vamana R=64, PQ M=32 in HBM, 512 B node blocks in host pinned memory, k=10"
 
