@@ -349,7 +349,7 @@ def run_ours(args, rank: int, world: int):
 
 
 def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
-                load: float = 0.7, seed: int = 7):
+                load: float = 0.7, seed: int = 7, Ls=None):
     """Continuous-batching request loop.  Requests are batches of queries with
     size log-uniform in [1, 512], k in {10, 100} and L in {L*, 1.25 L*, 1.5 L*}
     (L* = the batch operating point).  Phase 1 keeps the server saturated to
@@ -358,7 +358,9 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
     arrival (admission waits included) to its results in host memory."""
     import paper_2507_10070_b300 as ann
     rng = np.random.default_rng(seed)
-    Ls = [L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32]
+    if Ls is None:
+        Ls = [L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32]
+    Ls = [int(x) for x in Ls]
     nq_all = w["q"].shape[0]
 
     def draw(n):
@@ -653,6 +655,61 @@ def run_large(args):
     return out
 
 
+def run_serving_workload(args):
+    """Serving workload: 10^7 SIFT-like uint8 vectors (the 1M workload's
+    generator: 256 centres, sigma 20), 10,000 queries.  The degree selector
+    picks R among {32, 48, 64, 96} and the pipeline depth; Vamana at that R
+    is built on the GPU and stored breadth-first, with the node blocks in
+    host pinned memory and 32-byte PQ codes in HBM.  Requests arrive as a
+    seeded Poisson stream of batches (size log-uniform in [1, 512], k in
+    {10, 100}, L in {64, 128, 256}) at 70% of the measured capacity; the
+    batched QPS and recall at each L are reported beside it."""
+    import torch
+    import paper_2507_10070_b300 as ann
+    torch.cuda.set_device(0)
+    n, nq, M = args.serving_n, 10_000, 32
+    t0 = time.time()
+    at = ann.autotune_degree(degrees=(32, 48, 64, 96), n_sample=100_000, d=128, M=M, L=32, nq=4096, seed=1)
+    R, depth = min(at["degree"], 64), at["depth"]
+    mx = datagen.sift_like()
+    base, q = mx.base(n), mx.queries(nq)
+    cb, codes = ann.build_pq(base, M, n_train=100_000, iters=25,
+                             kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, M), encode_device="gpu")
+    adj, entry = ann.build_graph(base, R, 1.2, 128, seed=mx.seed, device="gpu")
+    gt_ids, gt_d = ann.knn_exact(base, q, 100)
+    b2, a2, e2, c2, old = ann.reorder_graph(base, adj, entry, codes)
+    del adj, codes
+    ix = ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
+    setup = time.time() - t0
+    qd = torch.from_numpy(q).cuda()
+    st = torch.cuda.Stream()
+    batch = {}
+    for L in (64, 128, 256):
+        for k in (10, 100):
+            ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+            dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+            ix.search_dev(qd, k, L, depth, ids, dists, stream=st)
+            ix.sync(st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(3):
+                ix.search_dev(qd, k, L, depth, ids, dists, stream=st)
+            e1.record(st)
+            ix.sync(st)
+            torch.cuda.synchronize()
+            r = ann.recall_at_k(ids.cpu().numpy()[:, :10], gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy()[:, :10])
+            batch[f"L{L}_k{k}"] = {"qps": round(3 * nq / (e0.elapsed_time(e1) * 1e-3), 1),
+                                   "recall_at_10": round(r, 4)}
+    with ClockSampler(0) as clk:
+        serving = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], 128, depth,
+                              args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=(64, 128, 256))
+    ix.close()
+    return {"what": run_serving_workload.__doc__.split("\n\n")[0].replace("\n", " "),
+            "n": n, "nq": nq, "M": M, "R": R, "depth": depth, "autotune": at,
+            "batched": batch, "serving": serving, "clocks": clk.summary(),
+            "setup_s": round(setup, 1)}
+
+
 def cpu_baseline(w, L: int, sample: int):
     """The CPU oracle as it stands (synchronous search, every host core) on the
     first `sample` queries of the same workload and index."""
@@ -732,6 +789,9 @@ def main():
                     help="only run the precision workload (float32 DEEP-like, BF16/FP8/PQ navigation)")
     ap.add_argument("--precision-n", type=int, default=10_000_000)
     ap.add_argument("--precision-Ls", type=int, nargs="+", default=[32, 64, 128, 256, 512])
+    ap.add_argument("--serving", action="store_true",
+                    help="only run the serving workload (10^7 uint8 vectors, autotuned R and depth)")
+    ap.add_argument("--serving-n", type=int, default=10_000_000)
     ap.add_argument("--large", action="store_true",
                     help="only run the large out-of-core workload (10^8 uint8 vectors by default)")
     ap.add_argument("--large-n", type=int, default=100_000_000)
@@ -747,6 +807,9 @@ def main():
         return
     if args.large:
         print(json.dumps(run_large(args)), flush=True)
+        return
+    if args.serving:
+        print(json.dumps(run_serving_workload(args)), flush=True)
         return
     if args.probe_sweep:
         import paper_2507_10070_b300 as ann
