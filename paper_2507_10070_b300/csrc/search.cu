@@ -1060,14 +1060,15 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   const WarpSmem lay = warp_smem_layout(mode, M, d, slot_bytes, depth, L, k, p.nb);
   p.smem_per_warp = lay.total;
   p.warps_per_block = 1;
-  // Visited table: 2^15 slots (2^16 beyond L = 2048), doubled for R > 64 and
-  // halved for R <= 32.  Measured on the 1M SIFT-like workload the largest
-  // visited set of 1,000 queries is ~12k nodes up to L = 2048 and ~18.5k at
-  // L = 4096 (R = 64), so the 3/4-load overflow limit leaves a >= 2x margin,
-  // while 128 KB per warp keeps the tables of all resident warps in L2.
+  // Visited table: 2^15 slots (2^16 beyond L = 2048), doubled for R > 64.
+  // Measured on the 1M SIFT-like workload the largest visited set of 1,000
+  // queries is ~12k nodes up to L = 2048 and ~18.5k at L = 4096 (R = 64), so
+  // the 3/4-load overflow limit leaves a >= 2x margin, while 128 KB per warp
+  // keeps the tables of the resident warps in L2.  Smaller degrees keep the
+  // same size: at 10^7 nodes and R = 32 a query at L = 256 visited more than
+  // the 12,288 nodes a halved table would hold.
   int lg = L <= 2048 ? 15 : 16;
   if (R > 64) ++lg;
-  if (R <= 32) --lg;
   p.vis_log2 = lg;
   p.vis_log_cap = (3 << lg) / 4 + 32 * p.nb + 1;
   int dev = 0, sms = 0, per_sm = 0;
