@@ -11,9 +11,13 @@ numpy-facing wrappers.  Parity status per function:
 * knn, l2, medoid, search (every depth): pinned by closed forms, brute force
   on tiny inputs and hand-traced graphs (tests/test_oracle_*.py,
   tests/golden/).
-* pq_train, vamana: parity unpinned -- only invariants are checked (Lloyd
-  distortion non-increasing, k-means++ picks on hand-made data; graph degree
-  bound, no self loops, connectivity, recall).
+* pq_train: K=1 closed forms (the k-means++ pick, the mean) and Lloyd's
+  iterations against scipy's kmeans2 from the same start (float data); the
+  integer rounding for uint8 data by invariants.
+* vamana: a closed form (points on a line with complete candidate sets and
+  alpha = 1 give the path graph) and graph invariants (degree bound, no self
+  loops, connectivity, recall); alpha > 1 on squared distances only by
+  those invariants.
 """
 from __future__ import annotations
 

@@ -16,15 +16,17 @@
  *                   medoid; the paper only says "entrance node").
  *   orc_pq_train    product-quantiser codebook: k-means++ seeding + Lloyd
  *                   iterations per subspace (PQ codes "in memory", Section
- *                   "Graph-Based Vector Indexing").  Parity unpinned beyond
- *                   the invariants the tests check (distortion monotone,
- *                   reduction to plain k-means on tiny inputs).
+ *                   "Graph-Based Vector Indexing").  Pinned: K=1 closed
+ *                   forms, and Lloyd's steps against scipy's kmeans2 from
+ *                   the same start (float data).
  *   orc_pq_encode   nearest-centroid code per subspace, lowest index on ties.
  *   orc_vamana      Vamana graph (DiskANN's index, which the paper builds on):
  *                   random R-regular start, two passes (alpha=1, then alpha,
  *                   alpha compared with squared distances),
- *                   GreedySearch + RobustPrune + back-edges.  Parity
- *                   unpinned: only graph invariants are checked.
+ *                   GreedySearch + RobustPrune + back-edges.  Pinned by
+ *                   a closed form (points on a line, complete candidates,
+ *                   alpha = 1: the path graph) and graph invariants; the
+ *                   squared-distance reading of alpha only by invariants.
  *   orc_search      best-first search with a dependency-relaxed fetch
  *                   schedule of depth D (Sections "Data-Dependency in
  *                   Traditional Best-First Search" and "Dependency Relaxed

@@ -138,6 +138,25 @@ def test_pq_train_distortion_non_increasing_and_integer_centroids():
     assert cb.min() >= 0 and cb.max() <= 255
 
 
+@pytest.mark.parametrize("iters", [1, 3, 8])
+def test_pq_train_lloyd_matches_scipy_kmeans2(iters):
+    """Lloyd's iterations pinned to an independent implementation: from the
+    oracle's own k-means++ start (iters=0), scipy's kmeans2 run for the same
+    number of assign-and-update steps gives the same centroids (float32
+    data, no empty clusters, so the oracle's empty-cluster rule is idle)."""
+    from scipy.cluster.vq import kmeans2
+    mx = datagen.inmemory_f32(d=16)
+    x = mx.base(6000)
+    M, K = 4, 256
+    u = datagen.kmeanspp_uniforms(mx.seed, M, K)
+    start = oracle.pq_train(x, M, u, iters=0, round_int=False)
+    cb = oracle.pq_train(x, M, u, iters=iters, round_int=False)
+    for m in range(M):
+        sub = x[:, 4 * m:4 * (m + 1)].astype(np.float64)
+        ref, _ = kmeans2(sub, start[m].astype(np.float64), iter=iters, minit="matrix", missing="raise")
+        assert np.allclose(cb[m], ref, rtol=1e-6, atol=1e-6)
+
+
 def test_pq_navigation_hand_worked_star():
     g = load_golden("pq_star5.json")
     base = np.array(g["vectors"], np.uint8)
@@ -216,6 +235,36 @@ def small_f32():
                         datagen.random_out_neighbours(mx.seed, 3000, 24))
     gi, gd = oracle.knn(base, q, 10)
     return base, q, med, adj, gi, gd
+
+
+@pytest.mark.parametrize("n,seed", [(10, 1), (40, 2), (120, 3)])
+def test_vamana_on_a_line_is_the_path_graph(n, seed):
+    """A closed form.  Points on a line (ids shuffled), a complete start graph
+    (R = n-1) and L_build = n, so every search visits every node: with
+    alpha = 1 the prune keeps, on each side, only the nearest point (it
+    occludes everything beyond it), and back edges can only re-add those two.
+    The result is the path graph.  With alpha = 1.2 far points survive the
+    prune, so the same check must fail there."""
+    rng = np.random.default_rng(seed)
+    pts = np.zeros((n, 16), np.float32)
+    pts[:, 0] = rng.permutation(rng.choice(np.arange(10000), n, replace=False)).astype(np.float32)
+    entry = oracle.medoid(pts)
+    order = np.argsort(pts[:, 0])
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+
+    def path_mismatches(alpha):
+        adj = oracle.vamana(pts, n - 1, alpha, n, entry, datagen.build_order(seed, n),
+                            datagen.random_out_neighbours(seed, n, n - 1))
+        bad = 0
+        for i in range(n):
+            r = rank[i]
+            want = {int(order[j]) for j in (r - 1, r + 1) if 0 <= j < n}
+            bad += {int(v) for v in adj[i] if v >= 0} != want
+        return bad
+
+    assert path_mismatches(1.0) == 0
+    assert path_mismatches(1.2) > 0
 
 
 def test_vamana_graph_invariants(small_f32):
