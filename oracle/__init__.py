@@ -14,10 +14,10 @@ numpy-facing wrappers.  Parity status per function:
 * pq_train: K=1 closed forms (the k-means++ pick, the mean) and Lloyd's
   iterations against scipy's kmeans2 from the same start (float data); the
   integer rounding for uint8 data by invariants.
-* vamana: a closed form (points on a line with complete candidate sets and
-  alpha = 1 give the path graph) and graph invariants (degree bound, no self
-  loops, connectivity, recall); alpha > 1 on squared distances only by
-  those invariants.
+* vamana: closed forms on a line with complete candidate sets (alpha = 1
+  gives the path graph; alpha > 1 gives the ladder of kept distances that
+  alpha on squared distances implies) and graph invariants (degree bound, no
+  self loops, connectivity, recall).
 """
 from __future__ import annotations
 

@@ -25,8 +25,8 @@
  *                   alpha compared with squared distances),
  *                   GreedySearch + RobustPrune + back-edges.  Pinned by
  *                   a closed form (points on a line, complete candidates,
- *                   alpha = 1: the path graph) and graph invariants; the
- *                   squared-distance reading of alpha only by invariants.
+ *                   alpha = 1: the path graph; alpha > 1: the ladder that
+ *                   alpha on squared distances gives) and graph invariants.
  *   orc_search      best-first search with a dependency-relaxed fetch
  *                   schedule of depth D (Sections "Data-Dependency in
  *                   Traditional Best-First Search" and "Dependency Relaxed

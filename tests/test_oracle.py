@@ -267,6 +267,44 @@ def test_vamana_on_a_line_is_the_path_graph(n, seed):
     assert path_mismatches(1.2) > 0
 
 
+@pytest.mark.parametrize("alpha", [1.2, 2.0])
+def test_vamana_alpha_is_on_squared_distances(alpha):
+    """A closed form for the prune with alpha > 1.  The node processed last in
+    the second pass keeps exactly its prune result.  With complete candidates
+    on a line, a point at distance b on one side is occluded by a kept point
+    at distance a < b on that side iff alpha (b - a)^2 <= b^2, i.e. b <= c a
+    with c = sqrt(alpha) / (sqrt(alpha) - 1): the kept distances form a
+    ladder, each the first beyond c times the previous.  Comparing alpha with
+    plain distances would give c = alpha / (alpha - 1), a different ladder at
+    alpha = 1.2 (6 instead of 11.5)."""
+    right, left = [1, 7, 13, 80, 150, 1000], [2, 15, 30, 400, 3000]
+    xs = [0.0] + right + [-v for v in left]
+    n = len(xs)
+    perm = np.random.default_rng(4).permutation(n)
+    pts = np.zeros((n, 16), np.float32)
+    pts[perm, 0] = np.array(xs, np.float32)
+    p = int(perm[0])
+    order = np.array([i for i in datagen.build_order(3, n) if i != p] + [p], np.int32)
+    adj = oracle.vamana(pts, n - 1, alpha, n, oracle.medoid(pts), order,
+                        datagen.random_out_neighbours(3, n, n - 1))
+    got = sorted(float(pts[v, 0]) for v in adj[p] if v >= 0)
+
+    def ladder(ds, c):
+        kept = []
+        for b in sorted(ds):
+            if not kept or b > c * kept[-1]:
+                kept.append(b)
+        return kept
+
+    c_sq = np.sqrt(alpha) / (np.sqrt(alpha) - 1)
+    want = sorted([float(b) for b in ladder(right, c_sq)] + [-float(b) for b in ladder(left, c_sq)])
+    assert got == want
+    if alpha == 1.2:
+        c_plain = alpha / (alpha - 1)
+        plain = sorted([float(b) for b in ladder(right, c_plain)] + [-float(b) for b in ladder(left, c_plain)])
+        assert plain != want
+
+
 def test_vamana_graph_invariants(small_f32):
     base, q, med, adj, _, _ = small_f32
     assert adj.shape == (3000, 24)
