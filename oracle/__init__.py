@@ -11,9 +11,9 @@ numpy-facing wrappers.  Parity status per function:
 * knn, l2, medoid, search (every depth): pinned by closed forms, brute force
   on tiny inputs and hand-traced graphs (tests/test_oracle_*.py,
   tests/golden/).
-* pq_train: K=1 closed forms (the k-means++ pick, the mean) and Lloyd's
-  iterations against scipy's kmeans2 from the same start (float data); the
-  integer rounding for uint8 data by invariants.
+* pq_train: K=1 closed forms (the k-means++ pick, the mean, the mean
+  rounded half to even for uint8 data) and Lloyd's iterations against
+  scipy's kmeans2 from the same start (float data).
 * vamana: closed forms on a line with complete candidate sets (alpha = 1
   gives the path graph; alpha > 1 gives the ladder of kept distances that
   alpha on squared distances implies) and graph invariants (degree bound, no

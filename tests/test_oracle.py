@@ -115,6 +115,12 @@ def test_pq_train_single_centroid_closed_forms():
     cb1 = oracle.pq_train(x, 2, u, iters=1, K=1, round_int=False)
     assert np.allclose(cb1[0, 0], x[:, :2].mean(0), rtol=1e-6)
     assert np.allclose(cb1[1, 0], x[:, 2:].mean(0), rtol=1e-6)
+    # uint8 data (reading 9): the mean rounded half to even
+    cbr = oracle.pq_train(x, 2, u, iters=1, K=1, round_int=True)
+    assert np.array_equal(cbr[0, 0], np.rint(x[:, :2].mean(0))) and np.array_equal(cbr[1, 0], np.rint(x[:, 2:].mean(0)))
+    two = np.array([[1, 2, 3, 4], [2, 5, 6, 7]], np.uint8)      # means 1.5, 3.5, 4.5, 5.5
+    cbh = oracle.pq_train(two, 1, np.full((1, 1), 0.0), iters=1, K=1, round_int=True)
+    assert cbh[0, 0].tolist() == [2.0, 4.0, 4.0, 6.0]          # half to even (half up would give 5 at 4.5)
 
 
 def test_pq_train_recovers_exact_blobs():
