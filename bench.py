@@ -732,11 +732,13 @@ def cpu_baseline(w, L: int, sample: int):
 
 def run_reference(args):
     """The oracle arm: each step searches a bounded sample of the queries on
-    the host cores (synchronous best-first search, same index).  L is chosen by
-    the GPU arm's rule (smallest L with recall@10 >= 0.95), judged on the first
-    200 queries against the oracle's own brute-force ground truth."""
+    the host cores (synchronous best-first search).  Its index (same workload,
+    R, PQ and build parameters) is built by the library's host tooling, so no
+    CUDA code runs on this arm.  L is chosen by the GPU arm's rule (smallest L
+    with recall@10 >= 0.95), judged on the first 200 queries against the
+    oracle's own brute-force ground truth."""
     import oracle
-    w = prepare_sift_like(args.n, args.nq, builder=args.builder)
+    w = prepare_sift_like(args.n, args.nq, builder="cpu")
     threads = oracle.default_threads()
     qs = w["q"][:200]
     gi, gd = oracle.knn(w["base"], qs, 10, threads)
