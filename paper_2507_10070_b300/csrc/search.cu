@@ -376,6 +376,68 @@ __device__ __forceinline__ unsigned nav_dist_warp(const SearchArgs& a, const uns
   return __float_as_uint(warp_sum_f32(acc));
 }
 
+// Partial navigation distance for the grouped evaluation: this lane sums
+// chunks sub, sub + lpg, ... of node w's vector (a chunk is 4 coordinates);
+// the group then adds its lanes' partial sums.  Same arithmetic per chunk as
+// the warp-wide functions above.
+template <int MODE>
+__device__ __forceinline__ float nav_partial_f32(const SearchArgs& a, const unsigned char* qs, int w,
+                                                 int sub, int lpg) {
+  const float4* q = reinterpret_cast<const float4*>(qs);
+  const int chunks = a.d >> 2;
+  float acc = 0.f;
+  if (MODE == kModeExactF32) {
+    const float4* x = reinterpret_cast<const float4*>(static_cast<const float*>(a.vectors) +
+                                                      static_cast<size_t>(w) * a.d);
+    for (int j = sub; j < chunks; j += lpg) {
+      const float4 xv = __ldg(x + j), qv = q[j];
+      float t;
+      t = qv.x - xv.x; acc = fmaf(t, t, acc);
+      t = qv.y - xv.y; acc = fmaf(t, t, acc);
+      t = qv.z - xv.z; acc = fmaf(t, t, acc);
+      t = qv.w - xv.w; acc = fmaf(t, t, acc);
+    }
+  } else if (MODE == kModeBF16) {
+    const uint2* x = reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(a.nav) +
+                                                    static_cast<size_t>(w) * a.d);
+    for (int j = sub; j < chunks; j += lpg) {
+      const uint2 v = __ldg(x + j);
+      const float4 qv = q[j];
+      float t;
+      t = qv.x - __uint_as_float(v.x << 16); acc = fmaf(t, t, acc);
+      t = qv.y - __uint_as_float(v.x & 0xffff0000u); acc = fmaf(t, t, acc);
+      t = qv.z - __uint_as_float(v.y << 16); acc = fmaf(t, t, acc);
+      t = qv.w - __uint_as_float(v.y & 0xffff0000u); acc = fmaf(t, t, acc);
+    }
+  } else if (MODE == kModeFP8) {
+    const unsigned* x = reinterpret_cast<const unsigned*>(static_cast<const uint8_t*>(a.nav) +
+                                                          static_cast<size_t>(w) * a.d);
+    const float s = a.nav_inv_scale;
+    for (int j = sub; j < chunks; j += lpg) {
+      __nv_fp8x4_e4m3 f;
+      f.__x = __ldg(x + j);
+      const float4 xv = static_cast<float4>(f);
+      const float4 qv = q[j];
+      float t;
+      t = qv.x - xv.x * s; acc = fmaf(t, t, acc);
+      t = qv.y - xv.y * s; acc = fmaf(t, t, acc);
+      t = qv.z - xv.z * s; acc = fmaf(t, t, acc);
+      t = qv.w - xv.w * s; acc = fmaf(t, t, acc);
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ unsigned nav_partial_u8(const SearchArgs& a, const unsigned char* qs, int w,
+                                                   int sub, int lpg) {
+  const unsigned* x = reinterpret_cast<const unsigned*>(static_cast<const uint8_t*>(a.vectors) +
+                                                        static_cast<size_t>(w) * a.d);
+  const unsigned* q = reinterpret_cast<const unsigned*>(qs);
+  unsigned acc = 0;
+  for (int j = sub; j < (a.d >> 2); j += lpg) acc = sq4(q[j], __ldg(x + j), acc);
+  return acc;
+}
+
 // Navigation distance of node w for the non-PQ modes.
 template <int MODE>
 __device__ __forceinline__ unsigned navigation_dist(const SearchArgs& a, const unsigned char* qs,
@@ -671,16 +733,41 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
           }
         }
       } else {
+        // Vector modes: the warp splits into groups of lpg lanes (a power of
+        // two with at most 8 chunks per lane), each group summing one
+        // neighbour, so 32/lpg neighbours' gathers are in flight at once
+        // instead of one.  Per node the summation order is fixed by lpg.
+        const int chunks = a.d >> 2;
+        int lpg = 1;
+        while (lpg < 32 && lpg * 8 < chunks) lpg <<= 1;
+        const int groups = 32 / lpg;
+        const int grp = lane / lpg, sub = lane % lpg;
+        const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
           unsigned m = __ballot_sync(kFull, fresh[t] || pending[t]);
           while (m) {
-            const int src_lane = __ffs(m) - 1;
-            m &= m - 1;
-            const int id = __shfl_sync(kFull, w[t], src_lane);
-            const unsigned dist = navigation_dist<MODE>(a, qs, id, lane);
-            if (lane == src_lane) key[t] = make_key(dist, static_cast<unsigned>(id));
+            // group g evaluates the neighbour held by the g-th set lane of m
+            unsigned mm = m;
+            for (int i = 0; i < grp && mm; ++i) mm &= mm - 1;
+            const int src = mm ? __ffs(mm) - 1 : -1;
+            const int id = __shfl_sync(kFull, w[t], src < 0 ? 0 : src);
+            unsigned bits;
+            if (MODE == kModeExactU8) {
+              unsigned acc = src >= 0 ? nav_partial_u8(a, qs, id, sub, lpg) : 0u;
+              for (int off = lpg >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+              bits = acc;
+            } else {
+              float acc = src >= 0 ? nav_partial_f32<MODE>(a, qs, id, sub, lpg) : 0.f;
+              for (int off = lpg >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+              bits = __float_as_uint(acc);
+            }
+            // the neighbour's own lane takes its group's sum
+            const int r = __popc(m & lt_mask);
+            const unsigned got = __shfl_sync(kFull, bits, (r < groups ? r : 0) * lpg);
+            if (((m >> lane) & 1u) && r < groups) key[t] = make_key(got, static_cast<unsigned>(w[t]));
+            for (int i = 0; i < groups && m; ++i) m &= m - 1;
           }
         }
       }
