@@ -86,7 +86,9 @@ def ground_truth(w, k: int = 10):
         z = np.load(path)
         return z["ids"], z["dists"]
     ids, dists = ann.knn_exact(w["base"], w["q"], k)
-    np.savez(path, ids=ids, dists=dists)
+    tmp = path + f".{os.getpid()}.tmp.npz"   # ranks of one node share the cache: write atomically
+    np.savez(tmp, ids=ids, dists=dists)
+    os.replace(tmp, path)
     return ids, dists
 
 
@@ -471,7 +473,9 @@ def run_precision(args):
         cb, codes = ann.build_pq(base, 48, n_train=100_000, iters=25,
                                  kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, 48))
         gi, gd = ann.knn_exact(base, q, k)
-        np.savez(path, adj=adj, entry=entry, cb=cb, codes=codes, gi=gi, gd=gd)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, adj=adj, entry=entry, cb=cb, codes=codes, gi=gi, gd=gd)
+        os.replace(tmp, path)
     setup = time.time() - t0
     qd = torch.from_numpy(q).cuda()
     ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
