@@ -730,8 +730,9 @@ def cpu_baseline(w, L: int, sample: int):
     oracle.search(w["base"], w["adj"], w["entry"], q, 10, L, 0, codebook=w["cb"], codes=w["codes"],
                   threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(sample / dt, 1), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {sample} of the 10,000 queries, L={L}, depth 0, k=10"}
+    return {"value": round(len(q) / dt, 1), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": (f"all {len(q):,} queries" if len(q) == w["q"].shape[0] else
+                       f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f", L={L}, depth 0, k=10"}
 
 
 def run_reference(args):
@@ -762,7 +763,8 @@ def run_reference(args):
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     qps = len(q) * args.steps / sum(times)
-    sample = f"first {len(q)} of the 10,000 queries per step, L={L}, depth 0, k=10"
+    sample = (f"all {len(q):,} queries" if len(q) == w["q"].shape[0] else
+              f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f" per step, L={L}, depth 0, k=10"
     return {"impl": "reference", "metric": METRIC, "value": round(qps, 1), "unit": "queries/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(times) / args.steps, 3), "higher_is_better": True,
@@ -787,7 +789,8 @@ def main():
                     default=[32, 64, 128, 256, 512, 768, 1024, 1280, 1536, 2048, 3072, 4096])
     ap.add_argument("--depths", type=int, nargs="+", default=[0, 1, 2, 4])
     ap.add_argument("--target-recall", type=float, default=0.95)
-    ap.add_argument("--cpu-sample", type=int, default=2000)
+    ap.add_argument("--cpu-sample", type=int, default=10_000,
+                    help="queries the CPU oracle searches (per step on the reference arm)")
     ap.add_argument("--ref-L", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
