@@ -9,11 +9,15 @@ function follows in the paper); this module compiles it with gcc and exposes
 numpy-facing wrappers.  Parity status per function:
 
 * knn, l2, medoid, search (every depth): pinned by closed forms, brute force
-  on tiny inputs and hand-traced graphs (tests/test_oracle_*.py,
-  tests/golden/).
+  on tiny inputs and hand-traced graphs at depths 0, 1, 2 and 4
+  (tests/test_oracle*.py, tests/golden/).
 * pq_train: K=1 closed forms (the k-means++ pick, the mean, the mean
-  rounded half to even for uint8 data) and Lloyd's iterations against
-  scipy's kmeans2 from the same start (float data).
+  rounded half to even for uint8 data), hand-worked k-means++ seeding at
+  K=2 and K=3 (D^2 weighting, strict comparison), hand-worked empty-cluster
+  cases (farthest point, lowest id on ties, each point used once), and
+  Lloyd's iterations against scipy's kmeans2 from the same start (float
+  data).  tests/test_oracle_pins.py also plants each of these mistakes in a
+  copy of oracle.c and checks that a pin fails.
 * vamana: closed forms on a line with complete candidate sets (alpha = 1
   gives the path graph; alpha > 1 gives the ladder of kept distances that
   alpha on squared distances implies) and graph invariants (degree bound, no

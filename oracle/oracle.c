@@ -17,8 +17,9 @@
  *   orc_pq_train    product-quantiser codebook: k-means++ seeding + Lloyd
  *                   iterations per subspace (PQ codes "in memory", Section
  *                   "Graph-Based Vector Indexing").  Pinned: K=1 closed
- *                   forms, and Lloyd's steps against scipy's kmeans2 from
- *                   the same start (float data).
+ *                   forms, hand-worked seeding at K=2 and K=3, hand-worked
+ *                   empty clusters, and Lloyd's steps against scipy's
+ *                   kmeans2 from the same start (float data).
  *   orc_pq_encode   nearest-centroid code per subspace, lowest index on ties.
  *   orc_vamana      Vamana graph (DiskANN's index, which the paper builds on):
  *                   random R-regular start, two passes (alpha=1, then alpha,
@@ -31,6 +32,7 @@
  *                   schedule of depth D (Sections "Data-Dependency in
  *                   Traditional Best-First Search" and "Dependency Relaxed
  *                   Strategy"); D = 0 is the textbook synchronous search.
+ *                   Pinned by hand traces at D = 0, 1, 2 and 4.
  */
 #include <math.h>
 #include <pthread.h>
