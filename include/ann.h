@@ -74,7 +74,7 @@ typedef struct ann_index ann_index; /* opaque, owned by the library */
  *    compressed copies -- nav = ANN_NAV_BF16 or ANN_NAV_FP8 with M == 0, or
  *    float PQ with M > 0 (M % 16 == 0, M <= 64, d % M == 0, any float
  *    codebook) -- followed by an exact FP32 rerank of the top
- *    rerank_mult * k expanded candidates (at most 256, at most L).
+ *    rerank_mult * k expanded candidates (at most 512, at most L).
  * Limits: 1 <= n < 2^31, 4 <= d <= 512, 1 <= R <= 128, 0 <= entry < n; every
  * adjacency id is -1 or in [0, n) and a row ends at its first -1.
  */
@@ -156,9 +156,23 @@ int64_t ann_index_block_bytes(const ann_index* index);
 int64_t ann_index_size(const ann_index* index);
 
 /*
+ * Warps per query of later ann_search / ann_search_dev calls on this index:
+ * 1 (default) or a warp group of 2 or 4 (PQ navigation on uint8 data only,
+ * ANN_EINVAL otherwise).  The group shares one query's lookup table, list,
+ * fetch ring and visited set; warp 0 runs the relaxed pipeline (selection,
+ * fetches, waits) exactly as a single warp does, and for each expansion the
+ * warps split the node's neighbours and the merge of the new candidates.
+ * Results, step counts and the schedule do not depend on the setting, only
+ * the time a step takes.  The serving loop, the kernel-grained ablation and
+ * ann_search_dev_noalloc always use one warp per query.  ANN_EBUSY while a
+ * search runs on the index.
+ */
+int ann_set_warps_per_query(ann_index* index, int32_t warps);
+
+/*
  * Batched search, host buffers (the end-to-end call).
  *  queries: host, nq*d elements of the index's dtype.
- *  k: results per query, 1 <= k <= min(L, 256).   L: candidate list size, L <= 4096.
+ *  k: results per query, 1 <= k <= min(L, 256).   L: candidate list size, L <= 16384.
  *  depth: relaxed-pipeline depth 0..4 (fetches in flight beyond the one being
  *    expanded); 0 is synchronous best-first search.
  *  ids, dists: host, nq*k; the k expanded nodes with the smallest exact
@@ -217,14 +231,23 @@ int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
  * device array inside the library, which every GPU that loads the library
  * holds until the process exits.  The caller still passes queries and outputs
  * (device memory, as for ann_search_dev) and loads the index beforehand.
- *  - Limit: a call must fit the scratch of at least 32 warps; an (L, R) pair
- *    needing more than 16 MiB / 32 = 512 KiB per warp (R > 64 with
- *    L > 2048) is rejected with ANN_EINVAL.  At most 16 MiB / (per-warp
+ *  - Limit: a call must fit the scratch of at least 32 warps; a call whose
+ *    visited table and clear log need more than 16 MiB / 32 = 512 KiB per
+ *    warp is rejected with ANN_EINVAL (on indexes up to 2^21 nodes: R > 64
+ *    with L > 2048, or L > 4096; on larger indexes the table grows with
+ *    L * R, so L * R > 2^15 is rejected).  At most 16 MiB / (per-warp
  *    scratch) warps run, fewer than ann_search_dev may use, so throughput
  *    is lower.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress with that device current).  With CUDA's lazy
+ *    module loading (the default) that lookup is also what loads the
+ *    library's device code on the device and places the 16 MiB array there,
+ *    so the first call may allocate device memory: make it once per device
+ *    at start-up, before any stream capture and before the phase that must
+ *    not allocate (a call with nq = 0 does only this set-up).
+ *  - The address is kept for the life of the process: do not use this entry
+ *    point after cudaDeviceReset or after the device's primary context was
+ *    destroyed and created again.
  *  - Every call shares the one array and zeroes what must start at zero, so
  *    calls that overlap on the GPU race: serialise them (one stream, or
  *    events).
@@ -253,7 +276,7 @@ int ann_search_dev_noalloc(ann_index* index, const void* queries, int64_t nq, in
 typedef struct ann_server ann_server; /* opaque */
 
 typedef struct {
-  int32_t max_L;        /* largest L a request may use (sets the shared-memory layout), <= 4096 */
+  int32_t max_L;        /* largest L a request may use (sets the shared-memory layout), <= 16384 */
   int32_t max_k;        /* largest k, <= min(max_L, 256) */
   int32_t depth;        /* relaxed-pipeline depth 0..4 used for every query */
   int32_t slots;        /* staging ring size: queries queued or in flight at once */
@@ -380,8 +403,10 @@ int ann_build_graph(const void* base, int32_t dtype, int64_t n, int32_t d, int32
  * extra time per step with the blocks in host memory.  *best_degree is the
  * degree with the smallest |t_compute - t_fetch|; at that degree the pipeline
  * depth 0..4 with the highest measured queries/s is *best_depth, and the
- * five measured rates go to depth_qps (may be NULL).  Warps per query are
- * one in this kernel.  Uses the current device; takes seconds.
+ * five measured rates go to depth_qps (may be NULL); at that degree and
+ * depth the warps per query (1, 2 or 4, see ann_set_warps_per_query) with
+ * the highest measured queries/s is *best_warps, the three rates in
+ * warps_qps (may be NULL).  Uses the current device; takes seconds.
  */
 typedef struct {
   int32_t n_sample;        /* sample size (the paper suggests ~100k) */
@@ -403,7 +428,8 @@ typedef struct {
 } ann_autotune_point;
 
 int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
-                        int32_t* best_degree, int32_t* best_depth, float* depth_qps);
+                        int32_t* best_degree, int32_t* best_depth, float* depth_qps,
+                        int32_t* best_warps, float* warps_qps);
 
 /*
  * The same Vamana construction on the GPU (index-build tooling): the batch
@@ -432,12 +458,32 @@ int ann_encode_bf16(const float* x, int64_t n, uint16_t* out);
 int ann_encode_fp8e4m3(const float* x, int64_t n, float scale, uint8_t* out);
 
 /*
- * Exact k nearest neighbours by brute force on the GPU (ground truth).
+ * Exact k nearest neighbours by brute force on the GPU (ground truth for
+ * recall@k, Section "Evaluation Metrics").
  * base, queries: host; ids, dists: host, nq*k, ascending by (distance, id).
- * ANN_U8 distances are exact integers; ANN_F32 uses FP32.
+ * 1 <= k <= 128, n < 2^31.  ANN_U8 distances are exact integers; ANN_F32
+ * uses FP32.  uint8 data with d <= 128 runs on the tensor cores: the dot
+ * products of query and base tiles are BF16 x BF16 -> FP32 MMAs (tcgen05),
+ * exact for 8-bit integers, with the top-k selected from the accumulator in
+ * the same kernel; other data run on the CUDA cores.
  */
 int ann_knn_exact(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
                   int64_t nq, int32_t k, int32_t* ids, float* dists);
+
+/* Engines of ann_knn_exact_ex. */
+typedef enum {
+  ANN_KNN_AUTO = 0,         /* tensor cores where the data allow, else CUDA cores */
+  ANN_KNN_TENSOR_CORES = 1, /* uint8 data with d <= 128 only (ANN_EINVAL otherwise) */
+  ANN_KNN_CUDA_CORES = 2    /* the CUDA-core kernels (__dp4a for uint8, FP32 for float) */
+} ann_knn_engine;
+
+/* ann_knn_exact with an engine choice; *kernel_ms (may be NULL) receives
+ * the device time of the search itself (after the upload, before the
+ * download).  ANN_ETIMEOUT if a bounded wait of the tensor-core kernel ran
+ * out (results are then not valid). */
+int ann_knn_exact_ex(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
+                     int64_t nq, int32_t k, int32_t engine, int32_t* ids, float* dists,
+                     float* kernel_ms);
 
 /*
  * Storage-tier read probe: `iters` passes in which every warp of a persistent

@@ -115,6 +115,10 @@ class Index:
         except Exception:
             pass
 
+    def set_warps_per_query(self, w: int):
+        """Warps per query of later searches (1, 2 or 4; see ann_set_warps_per_query)."""
+        _check(_lib().ann_set_warps_per_query(self._h, int(w)))
+
     def _np_dtype(self):
         return np.uint8 if self.dtype == ANN_U8 else np.float32
 
@@ -301,20 +305,25 @@ def autotune_degree(degrees=(32, 48, 64, 96), n_sample: int = 100_000, d: int = 
                     M: int = 32, L: int = 32, nq: int = 4096, seed: int = 1):
     """The paper's computation / I/O balanced degree selector on random-link
     sample indices.  Returns a dict with the per-degree table, the chosen
-    degree (argmin |T_c - T_f|) and the fastest depth at that degree."""
+    degree (argmin |T_c - T_f|), the fastest depth at that degree and the
+    fastest warps per query (1, 2 or 4) at that degree and depth."""
     deg = np.ascontiguousarray(np.asarray(degrees, np.int32))
     cfg = _abi.AutotuneCfg(n_sample=n_sample, d=d, M=M, degrees=deg.ctypes.data,
                            n_degrees=len(deg), L=L, nq=nq, seed=seed)
     pts = (_abi.AutotunePoint * len(deg))()
-    best_d, best_depth = ctypes.c_int32(0), ctypes.c_int32(0)
+    best_d, best_depth, best_w = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     qps = np.zeros(5, np.float32)
+    wqps = np.zeros(3, np.float32)
     _check(_lib().ann_autotune_degree(ctypes.byref(cfg), pts, ctypes.byref(best_d),
-                                      ctypes.byref(best_depth), _p(qps)))
+                                      ctypes.byref(best_depth), _p(qps), ctypes.byref(best_w),
+                                      _p(wqps)))
     table = [{"degree": p.degree, "t_compute_us": round(p.t_compute_us, 3),
               "t_fetch_us": round(p.t_fetch_us, 3), "step_us_sync": round(p.step_us_sync, 3),
               "qps_sync": round(p.qps_sync, 1)} for p in pts]
     return {"table": table, "degree": best_d.value, "depth": best_depth.value,
-            "qps_by_depth": [round(float(x), 1) for x in qps], "warps_per_query": 1}
+            "qps_by_depth": [round(float(x), 1) for x in qps], "warps_per_query": best_w.value,
+            "qps_by_warps_per_query": {str(w): round(float(x), 1) for w, x in zip((1, 2, 4), wqps)},
+            "L": L}
 
 
 def encode_bf16(x):
@@ -354,16 +363,22 @@ def reorder_graph(base, adj, entry: int, codes=None):
     return base_out, adj_out, int(entry_out.value), codes_out, old_of_new
 
 
-def knn_exact(base, queries, k: int):
-    """Brute-force exact kNN on the GPU: (ids int32 (nq,k), dists float32 (nq,k))."""
+def knn_exact(base, queries, k: int, engine: str = "auto", return_ms: bool = False):
+    """Brute-force exact kNN on the GPU: (ids int32 (nq,k), dists float32 (nq,k)).
+    engine: "auto" (tensor cores for uint8 data with d <= 128, else CUDA
+    cores), "tensor" or "cuda".  With return_ms, also the device time of the
+    search itself in ms."""
     base = _c(base)
     queries = _c(queries, base.dtype)
     nq = queries.shape[0]
     ids = np.empty((nq, k), np.int32)
     dists = np.empty((nq, k), np.float32)
-    _check(_lib().ann_knn_exact(_p(base), _dtype_code(base), base.shape[0], base.shape[1],
-                                _p(queries), nq, k, _p(ids), _p(dists)))
-    return ids, dists
+    eng = {"auto": _abi.ANN_KNN_AUTO, "tensor": _abi.ANN_KNN_TENSOR_CORES,
+           "cuda": _abi.ANN_KNN_CUDA_CORES}[engine]
+    ms = ctypes.c_float(0.0)
+    _check(_lib().ann_knn_exact_ex(_p(base), _dtype_code(base), base.shape[0], base.shape[1],
+                                   _p(queries), nq, k, eng, _p(ids), _p(dists), ctypes.byref(ms)))
+    return (ids, dists, ms.value) if return_ms else (ids, dists)
 
 
 def probe_read_bandwidth(nbytes: int, block_bytes: int = 512, tier: int = ANN_TIER_HOST_PINNED,

@@ -12,16 +12,19 @@ ANN_U8, ANN_F32 = 0, 1
 ANN_TIER_HOST_PINNED, ANN_TIER_HBM = 0, 1
 ANN_NAV_AUTO, ANN_NAV_BF16, ANN_NAV_FP8 = 0, 1, 2
 
+ANN_KNN_AUTO, ANN_KNN_TENSOR_CORES, ANN_KNN_CUDA_CORES = 0, 1, 2
+
 STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA",
                 -4: "ANN_ETIMEOUT", -5: "ANN_EBUSY", -6: "ANN_EIO"}
 
 # Every symbol include/ann.h declares.
 EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_file",
            "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
+           "ann_set_warps_per_query",
            "ann_search", "ann_search_dev", "ann_sync", "ann_search_dev_noalloc",
            "ann_search_dev_kernel_grained",
            "ann_build_pq", "ann_build_graph",
-           "ann_knn_exact", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
+           "ann_knn_exact", "ann_knn_exact_ex", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
            "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3",
            "ann_pq_encode_gpu", "ann_reorder_graph"]
@@ -138,8 +141,13 @@ def lib():
         L.ann_reorder_graph.argtypes = [P, I32, I64, I32, I32, P, I32, P, I32, P, P, P, P, P]
         L.ann_pq_encode_gpu.restype = ctypes.c_int
         L.ann_pq_encode_gpu.argtypes = [P, I32, I64, I32, I32, P, P]
+        L.ann_set_warps_per_query.restype = ctypes.c_int
+        L.ann_set_warps_per_query.argtypes = [P, I32]
         L.ann_knn_exact.restype = ctypes.c_int
         L.ann_knn_exact.argtypes = [P, I32, I64, I32, P, I64, I32, P, P]
+        L.ann_knn_exact_ex.restype = ctypes.c_int
+        L.ann_knn_exact_ex.argtypes = [P, I32, I64, I32, P, I64, I32, I32, P, P,
+                                       ctypes.POINTER(ctypes.c_float)]
         L.ann_probe_read_bandwidth.restype = ctypes.c_int
         L.ann_probe_read_bandwidth.argtypes = [I64, I32, I32, I32, ctypes.POINTER(ctypes.c_double)]
         L.ann_serve_create.restype = ctypes.c_int
@@ -154,6 +162,7 @@ def lib():
         L.ann_autotune_degree.restype = ctypes.c_int
         L.ann_autotune_degree.argtypes = [ctypes.POINTER(AutotuneCfg), ctypes.POINTER(AutotunePoint),
                                           ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32), P,
                                           ctypes.POINTER(ctypes.c_int32), P]
         L.ann_serve_stats.restype = ctypes.c_int
         L.ann_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]

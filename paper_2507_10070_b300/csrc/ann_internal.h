@@ -28,7 +28,7 @@ __host__ __device__ constexpr bool mode_f32(int m) {
 }
 __host__ __device__ constexpr bool mode_pq(int m) { return m == kModePqU8 || m == kModePqF32; }
 
-constexpr int kMaxL = 4096;
+constexpr int kMaxL = 16384;
 constexpr int kMaxDepth = 4;
 constexpr int kMaxR = 128;
 constexpr int kMaxD = 512;
@@ -96,9 +96,11 @@ struct ServeArgs {
 struct SearchPlan {
   int mode;
   int nb;              // neighbour slots per lane: ceil(R/32) rounded to 1, 2 or 4
-  int smem_per_warp;   // bytes
+  int smem_per_warp;   // bytes of one query's state
   int warps_per_block;
+  int wpq;             // warps per query: 1, or 2 / 4 (one query per block, PQ mode)
   int blocks;          // grid size (persistent)
+  int tables;          // visited tables (and clear logs) the launch uses
   int vis_log2;
   int vis_log_cap;
 };
@@ -140,8 +142,11 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
 }
 
 // Plans and launches one batched search.  Returns cudaSuccess or the error.
+// n_index: nodes of the index (sizes the visited tables; 0 = small index).
+// wpq: warps per query requested (1, 2 or 4; more than 1 applies to PQ
+// navigation only).
 cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
-                        int64_t nq, SearchPlan* plan);
+                        int64_t nq, SearchPlan* plan, int64_t n_index = 0, int wpq = 1);
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream);
 // The same kernel as a cooperative launch (every block resident), for the
 // kernel-grained I/O ablation (a.grid_bar set).
@@ -160,9 +165,12 @@ cudaError_t launch_read_probe(const uint8_t* region, int64_t nblocks, int block_
                               unsigned long long* sink, cudaStream_t stream, float* ms_out,
                               int64_t* bytes_out);
 
-// Brute-force exact kNN (device buffers).
+// Brute-force exact kNN (device buffers).  engine: 0 = tensor cores where
+// the data allow (uint8, d <= 128), 1 = tensor cores only, 2 = CUDA cores.
+// *timed_out is set if a bounded wait of the tensor-core kernel ran out.
 cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, const void* queries,
-                             int64_t nq, int k, int32_t* ids, float* dists, cudaStream_t stream);
+                             int64_t nq, int k, int32_t* ids, float* dists, cudaStream_t stream,
+                             int engine, int* timed_out);
 
 // Error reporting (thread-local message).
 int set_error(int status, const char* fmt, ...);

@@ -71,9 +71,11 @@ int time_search(ann_index* ix, const std::vector<uint8_t>& q, int nq, int k, int
 
 extern "C" int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
                                    int32_t* best_degree, int32_t* best_depth,
-                                   float* depth_qps /* [5], may be NULL */) {
+                                   float* depth_qps /* [5], may be NULL */,
+                                   int32_t* best_warps, float* warps_qps /* [3], may be NULL */) {
   using ann::set_error;
-  if (!cfg || !points || !best_degree || !best_depth) return set_error(ANN_EINVAL, "ann_autotune_degree: NULL argument");
+  if (!cfg || !points || !best_degree || !best_depth || !best_warps)
+    return set_error(ANN_EINVAL, "ann_autotune_degree: NULL argument");
   if (cfg->n_sample < 1024 || cfg->d < 16 || cfg->d % 16 || cfg->M < 16 || cfg->M % 16 ||
       cfg->d % cfg->M || (cfg->d / cfg->M) % 4 || cfg->n_degrees < 1 || cfg->nq < 32 ||
       cfg->L < 10 || cfg->L > ann::kMaxL)
@@ -173,6 +175,23 @@ extern "C" int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_poi
       if (t.qps > best_q) {
         best_q = t.qps;
         *best_depth = depths[di];
+      }
+    }
+    // warps per query at that degree and depth: 1, 2 or 4, the highest
+    // measured throughput
+    double best_w = -1;
+    const int warps[3] = {1, 2, 4};
+    *best_warps = 1;
+    for (int wi = 0; wi < 3 && rc == ANN_OK; ++wi) {
+      rc = ann_set_warps_per_query(ix, warps[wi]);
+      if (rc != ANN_OK) break;
+      Timing t{};
+      rc = time_search(ix, q, nq, k, cfg->L, *best_depth, &t);
+      if (rc != ANN_OK) break;
+      if (warps_qps) warps_qps[wi] = static_cast<float>(t.qps);
+      if (t.qps > best_w) {
+        best_w = t.qps;
+        *best_warps = warps[wi];
       }
     }
     ann_free(ix);

@@ -1,6 +1,10 @@
 // Brute-force exact k nearest neighbours on the GPU (ground truth for recall).
 //
-// Two kernels per chunk of queries:
+// uint8 data with d <= 128 runs on the tensor cores (knn_tc_kernel below):
+// the dot products q.x are a dense contraction, and their BF16 x BF16 ->
+// FP32 products and sums are exact integers there, so the distances are
+// exact.  float32 data, and uint8 data with d > 128, take the CUDA-core
+// path, two kernels per chunk of queries:
 //  1. dist_tile: a 64-query x 64-row tile per block, 256 threads each owning
 //     a 4x4 sub-tile; query and base rows staged in shared memory.  uint8
 //     distances are exact integers (__vabsdiffu4 + __dp4a); float32 uses FP32.
@@ -10,7 +14,11 @@
 //     minimum), and one block per query merges the segments' candidates.
 // Keys are (distance bits << 32 | id): the order is (distance, id) because
 // non-negative float bit patterns sort like the floats they encode.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <mutex>
 
 #include "ann_internal.h"
 
@@ -138,9 +146,523 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Tensor-core path (uint8 data, d <= 128).
+//
+// distance(q, x) = |q|^2 + |x|^2 - 2 q.x.  The dot products of a tile of 128
+// queries (A, the MMA's M) with a tile of 128 base rows (B, its N) over the
+// d coordinates (K) run on tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulator in tensor memory).  uint8 values are exact in BF16, every
+// product is an integer below 2^16 and every partial sum an integer below
+// d * 255^2 <= 8,323,200 < 2^24, so FP32 accumulation is exact in any order;
+// the distance, below 2 * 8,323,200 < 2^24, is exact in FP32 as well.  The
+// top-k selection runs in the same kernel on the accumulator, so the
+// distance matrix never goes to HBM.
+//
+// Per CTA (one query tile x a contiguous range of base tiles), 12 warps:
+//   warp 0 (one lane)  TMA producer: the query tile once, then base tiles into
+//                      a ring of kStages shared-memory stages (128-byte
+//                      swizzled, one 64-coordinate "atom" = 128 B per row);
+//   warp 1 (one lane)  MMA issuer: d/16 MMAs per base tile into one of two
+//                      tensor-memory accumulators (128 lanes x 128 columns);
+//                      tcgen05.commit frees the stage and publishes the
+//                      accumulator;
+//   warps 4-7, 8-11    two epilogue warpgroups, one per accumulator: thread t
+//                      of warp w reads row 32*(w%4)+t (one query) with
+//                      tcgen05.ld and keeps that query's ascending top-k of
+//                      (distance, id) keys; a key enters only if it is below
+//                      the k-th (one compare per distance).
+// Each warpgroup writes its lists as one part; a fold kernel merges the parts
+// with the running top-k after each chunk of the base.
+// Every wait on an mbarrier is bounded: past ~2 s the CTA sets an abort flag,
+// every role leaves its loop, the producer waits (bounded) for the copies it
+// issued, tensor memory is freed, and the host sees the error word.
+
+constexpr int kTcM = 128;            // queries per CTA (MMA M)
+constexpr int kTcN = 128;            // base rows per tile (MMA N)
+constexpr int kTcStages = 4;         // base-tile ring
+constexpr int kAtomBytes = 128 * 128;  // one 64-coordinate BF16 atom of a 128-row tile
+constexpr int kTcThreads = 384;
+constexpr long long kTcWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+struct TcArgs {
+  const float* qn;          // [nq] query norms
+  const float* xn;          // [chunk_n] base-row norms of this chunk
+  int64_t nq;
+  int32_t chunk_n;          // rows of this chunk
+  int64_t id0;              // id of the chunk's first row
+  int32_t tiles;            // base tiles in the chunk
+  int32_t splits;           // CTAs per query tile
+  int32_t natoms;           // padded d / 64 (1 or 2)
+  int32_t k;
+  int32_t nslots;           // parts per query: 1 (running) + 2 * splits
+  unsigned long long* keys; // [nq][nslots][k]
+  int* error;               // set to 1 if a wait ran out
+};
+
+__device__ __forceinline__ uint32_t sh_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sh_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(sh_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `bar` with this parity; false if the CTA aborted or
+// the wait ran out (which aborts it).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if ((i & 63u) == 63u) {
+      if (*abort) return false;
+      if (clock64() - t0 > kTcWaitCycles) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Bounded wait that ignores the abort flag (draining copies after an abort).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity) && clock64() - t0 < kTcWaitCycles) {
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(sh_u32(dst)), "l"(map), "r"(sh_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout that the TMA writes: rows of 128 bytes, 8-row groups 1024
+// bytes apart (stride byte offset), descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;           // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;   // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;           // version
+  d |= static_cast<uint64_t>(2) << 61;           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              (static_cast<uint32_t>(kTcN >> 3) << 17) |
+                              (static_cast<uint32_t>(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(sh_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    knn_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
+                  TcArgs a) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  // 1024-byte alignment for the swizzled operand tiles
+  const uint32_t raw = sh_u32(tc_smem_raw);
+  unsigned char* smem = tc_smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  unsigned char* sA = smem;                                   // natoms x 16 KB
+  unsigned char* sB = smem + 2 * kAtomBytes;                  // kTcStages x natoms x 16 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * 2 * kAtomBytes);
+  uint64_t* full = bars;                    // [kTcStages]
+  uint64_t* empty = bars + kTcStages;       // [kTcStages]
+  uint64_t* a_full = bars + 2 * kTcStages;  // [1]
+  uint64_t* acc_full = a_full + 1;          // [2]
+  uint64_t* acc_empty = a_full + 3;         // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 5);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int natoms = a.natoms;
+  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kTcM;
+  const int s = blockIdx.y;
+  const int t_lo = static_cast<int>((static_cast<int64_t>(a.tiles) * s) / a.splits);
+  const int t_hi = static_cast<int>((static_cast<int64_t>(a.tiles) * (s + 1)) / a.splits);
+  const int my_tiles = t_hi - t_lo;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTcStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    mbar_init(a_full, 1);
+    mbar_init(acc_full + 0, 1);
+    mbar_init(acc_full + 1, 1);
+    mbar_init(acc_empty + 0, 4);
+    mbar_init(acc_empty + 1, 4);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {  // two accumulators of 128 columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(sh_u32(tmem_slot)), "r"(2 * kTcN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&qmap) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&xmap) : "memory");
+    mbar_expect_tx(a_full, natoms * kAtomBytes);
+    for (int at = 0; at < natoms; ++at)
+      tma_load_2d(sA + at * kAtomBytes, &qmap, a_full, 64 * at, static_cast<int>(q0));
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < my_tiles && ok; ++i) {
+      const int st = i % kTcStages;
+      const uint32_t ph = (i / kTcStages) & 1;
+      if (!mbar_wait(empty + st, ph ^ 1u, abort)) { ok = false; break; }
+      mbar_expect_tx(full + st, natoms * kAtomBytes);
+      const int row = (t_lo + i) * kTcN;
+      for (int at = 0; at < natoms; ++at)
+        tma_load_2d(sB + (st * 2 + at) * kAtomBytes, &xmap, full + st, 64 * at, row);
+      issued = i + 1;
+    }
+    if (!ok) {
+      // let the copies still in flight land before the CTA exits
+      mbar_drain(a_full, 0);
+      for (int i = issued - kTcStages < 0 ? 0 : issued - kTcStages; i < issued; ++i)
+        mbar_drain(full + (i % kTcStages), (i / kTcStages) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    if (mbar_wait(a_full, 0, abort)) {
+      tc_fence_after();
+      const uint32_t a_base = sh_u32(sA);
+      for (int i = 0; i < my_tiles; ++i) {
+        const int st = i % kTcStages;
+        const uint32_t ph = (i / kTcStages) & 1;
+        const int b = i & 1;
+        const uint32_t u = static_cast<uint32_t>(i >> 1);
+        if (!mbar_wait(acc_empty + b, (u & 1u) ^ 1u, abort)) break;
+        if (!mbar_wait(full + st, ph, abort)) break;
+        tc_fence_after();
+        const uint32_t b_base = sh_u32(sB + st * 2 * kAtomBytes);
+        const uint32_t d_tmem = tmem + static_cast<uint32_t>(b * kTcN);
+        for (int at = 0; at < natoms; ++at)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            // a 16-coordinate step inside a 128-byte swizzled row is 32 bytes
+            const uint64_t ad = sw128_desc(a_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
+            const uint64_t bd = sw128_desc(b_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
+            tc_mma(d_tmem, ad, bd, (at | kk) != 0);
+          }
+        tc_commit(empty + st);
+        tc_commit(acc_full + b);
+      }
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: one query per thread, its running top-k in local memory
+    const int e = (warp - 4) >> 2;  // warpgroup = accumulator
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int64_t gq = q0 + row;
+    const bool live = gq < a.nq;
+    const float qn = live ? __ldg(a.qn + gq) : 0.f;
+    const int k = a.k;
+    unsigned long long top[kMaxK];
+    int have = 0;
+    unsigned long long thr = ~0ull;
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    for (int i = e; i < my_tiles; i += 2) {
+      const uint32_t u = static_cast<uint32_t>(i >> 1);
+      // one lane waits, so the warp stays converged for tcgen05.ld
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(acc_full + e, u & 1u, abort) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      tc_fence_after();
+      const int col0 = (t_lo + i) * kTcN;
+#pragma unroll 1
+      for (int c = 0; c < kTcN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + lane_base + static_cast<uint32_t>(e * kTcN + c * 32), r);
+        const int j0 = col0 + c * 32;
+        // the 32 base norms of this chunk: one coalesced load, then shuffles
+        const float xv = (j0 + lane < a.chunk_n) ? __ldg(a.xn + j0 + lane) : 0.f;
+        const unsigned thr_d = static_cast<unsigned>(thr >> 32);
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float x = __shfl_sync(0xffffffffu, xv, j);
+          const float dist = fmaf(-2.f, __uint_as_float(r[j]), qn + x);
+          // columns past the chunk can never enter
+          r[j] = (j0 + j < a.chunk_n) ? static_cast<unsigned>(dist) : 0xffffffffu;
+          any |= r[j] <= thr_d;
+        }
+        if (!live || !any) continue;  // the common case: nothing below the k-th
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j0 + j >= a.chunk_n) break;
+          const unsigned long long key =
+              (static_cast<unsigned long long>(r[j]) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
+          if (key < thr) {
+            int p = have < k ? have : k - 1;
+            while (p > 0 && top[p - 1] > key) {
+              top[p] = top[p - 1];
+              --p;
+            }
+            top[p] = key;
+            if (have < k) ++have;
+            if (have == k) thr = top[k - 1];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty + e);
+    }
+    if (live) {
+      unsigned long long* out =
+          a.keys + (static_cast<size_t>(gq) * a.nslots + 1 + 2 * s + e) * static_cast<size_t>(k);
+      for (int j = 0; j < k; ++j) out[j] = j < have ? top[j] : ~0ull;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0 && *abort) atomicExch(a.error, 1);
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcN)
+                 : "memory");
+  }
+}
+
+// uint8 rows -> BF16 rows zero-padded to dp coordinates, and each row's
+// squared norm (an exact integer in FP32).  One warp per row.
+__global__ void to_bf16_rows(const uint8_t* __restrict__ x, int64_t rows, int d, int dp,
+                             uint16_t* __restrict__ out, float* __restrict__ norms) {
+  const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const uint8_t* src = x + r * d;
+  uint16_t* dst = out + r * dp;
+  unsigned sq = 0;
+  for (int j = lane; j < dp; j += 32) {
+    const unsigned v = j < d ? src[j] : 0u;
+    sq += v * v;
+    dst[j] = static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);  // exact
+  }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) norms[r] = static_cast<float>(sq);
+}
+
+// Merge the parts of every query into its running top-k (slot 0) and clear
+// the parts for the next chunk.
+__global__ void __launch_bounds__(256) topk_fold(unsigned long long* __restrict__ keys, int nslots, int k) {
+  __shared__ unsigned long long best[kMaxK];
+  unsigned long long* p = keys + static_cast<size_t>(blockIdx.x) * nslots * k;
+  block_topk([&](int64_t i) { return p[i]; }, static_cast<int64_t>(nslots) * k, k, best);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nslots * k; i += blockDim.x) p[i] = i < k ? best[i] : ~0ull;
+}
+
+// Keys of slot 0 -> ids and exact integer distances.
+__global__ void topk_write(const unsigned long long* __restrict__ keys, int64_t nq, int nslots, int k,
+                           int32_t* __restrict__ ids, float* __restrict__ dists) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nq * k) return;
+  const int64_t q = i / k, j = i % k;
+  const unsigned long long b = keys[static_cast<size_t>(q) * nslots * k + j];
+  const bool ok = b != ~0ull;
+  ids[i] = ok ? static_cast<int32_t>(b & 0xffffffffu) : -1;
+  dists[i] = ok ? static_cast<float>(static_cast<unsigned>(b >> 32)) : __int_as_float(0x7f800000);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D map of `rows` BF16 rows of dp coordinates, 64 x 128 boxes, 128-byte
+// swizzle; rows past the end read as zero.
+bool bf16_row_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(dp), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(dp) * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr size_t kTcSmem = 1024 + 2 * kAtomBytes + kTcStages * 2 * kAtomBytes + 256;
+
 }  // namespace
 
-cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, const void* queries,
+// Exact kNN of uint8 data on the tensor cores (d <= 128, k <= 128), device
+// buffers.  The base is processed in chunks of up to 2^22 rows, each
+// converted to BF16 into one scratch buffer.
+cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* queries, int64_t nq, int k,
+                         int32_t* ids, float* dists, cudaStream_t stream, int* timed_out) {
+  if (d > 128 || k > kMaxK || n >= (1ll << 31)) return cudaErrorInvalidValue;
+  if (timed_out) *timed_out = 0;
+  if (nq == 0) return cudaSuccess;
+  const int dp = d <= 64 ? 64 : 128;
+  const int natoms = dp / 64;
+  const int64_t chunk = n < (1ll << 22) ? n : (1ll << 22);
+  const int64_t qtiles = (nq + kTcM - 1) / kTcM;
+  const int max_tiles = static_cast<int>((chunk + kTcN - 1) / kTcN);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // enough CTAs for a few waves of one CTA per SM, each over >= 8 tiles
+  int splits = static_cast<int>((4ll * sms + qtiles - 1) / qtiles);
+  if (splits > max_tiles / 8) splits = max_tiles / 8;
+  if (splits < 1) splits = 1;
+  const int nslots = 1 + 2 * splits;
+  uint16_t *qb = nullptr, *xb = nullptr;
+  float *qn = nullptr, *xn = nullptr;
+  unsigned long long* keys = nullptr;
+  int* err = nullptr;
+  // row buffers hold at least one full 128-row box (zero rows past the data)
+  const int64_t q_rows = nq > kTcM ? nq : kTcM;
+  const int64_t x_rows = chunk > kTcN ? chunk : kTcN;
+  cudaError_t e = cudaMalloc(&qb, static_cast<size_t>(q_rows) * dp * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(qb, 0, static_cast<size_t>(q_rows) * dp * 2, stream);
+  if (e == cudaSuccess) e = cudaMalloc(&qn, static_cast<size_t>(nq) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&xb, static_cast<size_t>(x_rows) * dp * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&xn, static_cast<size_t>(chunk) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&keys, static_cast<size_t>(nq) * nslots * k * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, static_cast<size_t>(nq) * nslots * k * 8, stream);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTcSmem));
+  CUtensorMap qmap, xmap;
+  if (e == cudaSuccess) {
+    to_bf16_rows<<<static_cast<unsigned>((nq * 32 + 255) / 256), 256, 0, stream>>>(queries, nq, d, dp, qb, qn);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && !bf16_row_map(&qmap, qb, q_rows, dp)) e = cudaErrorInvalidValue;
+  for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
+    const int64_t cn = (n - c0 < chunk) ? n - c0 : chunk;
+    const int64_t map_rows = cn > kTcN ? cn : kTcN;
+    if (cn < kTcN) {
+      e = cudaMemsetAsync(xb + cn * dp, 0, static_cast<size_t>(kTcN - cn) * dp * 2, stream);
+      if (e != cudaSuccess) break;
+    }
+    to_bf16_rows<<<static_cast<unsigned>((cn * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn, d, dp,
+                                                                                 xb, xn);
+    if (!bf16_row_map(&xmap, xb, map_rows, dp)) {
+      e = cudaErrorInvalidValue;
+      break;
+    }
+    TcArgs ta;
+    ta.qn = qn;
+    ta.xn = xn;
+    ta.nq = nq;
+    ta.chunk_n = static_cast<int32_t>(cn);
+    ta.id0 = c0;
+    ta.tiles = static_cast<int32_t>((cn + kTcN - 1) / kTcN);
+    ta.splits = splits < ta.tiles ? splits : ta.tiles;
+    ta.natoms = natoms;
+    ta.k = k;
+    ta.nslots = nslots;
+    ta.keys = keys;
+    ta.error = err;
+    knn_tc_kernel<<<dim3(static_cast<unsigned>(qtiles), static_cast<unsigned>(ta.splits)), kTcThreads, kTcSmem,
+                    stream>>>(qmap, xmap, ta);
+    topk_fold<<<static_cast<unsigned>(nq), 256, 0, stream>>>(keys, nslots, k);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    topk_write<<<static_cast<unsigned>((nq * k + 255) / 256), 256, 0, stream>>>(keys, nq, nslots, k, ids, dists);
+    e = cudaGetLastError();
+  }
+  int h_err = 0;
+  cudaError_t e2 = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && err) e = cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (timed_out) *timed_out = h_err;
+  cudaFree(qb);
+  cudaFree(qn);
+  cudaFree(xb);
+  cudaFree(xn);
+  cudaFree(keys);
+  cudaFree(err);
+  return e;
+}
+
+cudaError_t knn_exact_cuda_cores(const void* base, int dtype, int64_t n, int d, const void* queries,
                              int64_t nq, int k, int32_t* ids, float* dists, cudaStream_t stream) {
   if (k > kMaxK) return cudaErrorInvalidValue;
   const bool u8 = dtype == ANN_U8;
@@ -181,6 +703,20 @@ cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, cons
   cudaFree(dmat);
   cudaFree(part);
   return e != cudaSuccess ? e : e2;
+}
+
+// Engine choice: 0 = tensor cores where the data allow (uint8, d <= 128),
+// 1 = tensor cores (uint8, d <= 128 only), 2 = CUDA cores.
+cudaError_t knn_exact_device(const void* base, int dtype, int64_t n, int d, const void* queries,
+                             int64_t nq, int k, int32_t* ids, float* dists, cudaStream_t stream,
+                             int engine, int* timed_out) {
+  if (timed_out) *timed_out = 0;
+  const bool tc_ok = dtype == ANN_U8 && d <= 128 && k <= kMaxK;
+  if (engine == 1 && !tc_ok) return cudaErrorInvalidValue;
+  if (engine != 2 && tc_ok)
+    return knn_exact_tc(static_cast<const uint8_t*>(base), n, d, static_cast<const uint8_t*>(queries), nq, k,
+                        ids, dists, stream, timed_out);
+  return knn_exact_cuda_cores(base, dtype, n, d, queries, nq, k, ids, dists, stream);
 }
 
 }  // namespace ann

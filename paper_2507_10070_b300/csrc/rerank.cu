@@ -9,12 +9,12 @@
 namespace ann {
 namespace {
 
-constexpr int kRerankMax = 256;
+constexpr int kRerankMax = 512;
 
 __global__ void rerank_kernel(const float* __restrict__ vectors, int d, const float* __restrict__ queries,
                               int nq, const int32_t* __restrict__ cand, const int32_t* __restrict__ id_map,
                               int kc, int k, int32_t* __restrict__ ids, float* __restrict__ dists) {
-  __shared__ unsigned long long keys[4][kRerankMax];
+  __shared__ unsigned long long keys[4][kRerankMax];  // 16 KB
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int qi = blockIdx.x * 4 + wib;
   if (qi >= nq) return;  // warp-uniform

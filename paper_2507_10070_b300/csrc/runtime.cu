@@ -78,6 +78,7 @@ struct ann_index {
   void* nav = nullptr;       // BF16 / FP8 navigation copies
   float nav_inv_scale = 1.f;
   int rerank_mult = 4;
+  int wpq = 1;               // warps per query of ann_search / ann_search_dev (PQ mode)
   DevBuf rr_ids, rr_d;       // candidates before the exact rerank
   DevBuf grid_bar;           // kernel-grained I/O ablation: grid barrier state
   void* vectors = nullptr;
@@ -204,6 +205,16 @@ const char* ann_version(void) { return "libann 0.1 (sm_103a)"; }
 
 int64_t ann_index_block_bytes(const ann_index* ix) { return ix ? ix->block_bytes : 0; }
 int64_t ann_index_size(const ann_index* ix) { return ix ? ix->n : 0; }
+
+int ann_set_warps_per_query(ann_index* ix, int32_t w) {
+  if (!ix) return set_error(ANN_EINVAL, "index is NULL");
+  if (w != 1 && w != 2 && w != 4) return set_error(ANN_EINVAL, "warps per query must be 1, 2 or 4 (got %d)", w);
+  if (w > 1 && ix->mode != kModePqU8)
+    return set_error(ANN_EINVAL, "a warp group per query needs PQ navigation on uint8 data");
+  if (ix->busy.load()) return set_error(ANN_EBUSY, "the index is in use by a search");
+  ix->wpq = w;
+  return ANN_OK;
+}
 
 void ann_free(ann_index* ix) { release(ix); }
 
@@ -382,7 +393,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   int32_t* ids_out = ids;
   float* dists_out = dists;
   if (rr) {
-    k = std::min(L, std::min(256, std::max(k, ix->rerank_mult * k)));
+    k = std::min(L, std::min(512, std::max(k, ix->rerank_mult * k)));
     cudaError_t e1 = ix->rr_ids.ensure((size_t)nq * k * 4);
     if (e1 == cudaSuccess) e1 = ix->rr_d.ensure((size_t)nq * k * 4);
     if (e1 != cudaSuccess) return cuda_error(e1, "rerank buffers");
@@ -390,9 +401,10 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
     dists = static_cast<float*>(ix->rr_d.p);
   }
   SearchPlan plan;
-  cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan);
+  cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan, ix->n,
+                              kernel_grained ? 1 : ix->wpq);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
-  const size_t want = ((size_t)plan.blocks * plan.warps_per_block) << plan.vis_log2;
+  const size_t want = ((size_t)plan.tables) << plan.vis_log2;
   if (want > ix->vis_words) {
     // tables must start all-zero; the kernel clears after each query
     cudaError_t s = cudaStreamSynchronize(st);
@@ -406,7 +418,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
     if (e != cudaSuccess) return cuda_error(e, "cudaMemset visited tables");
     ix->vis_words = want;
   }
-  const size_t log_bytes = (size_t)plan.blocks * plan.warps_per_block * plan.vis_log_cap * 4;
+  const size_t log_bytes = (size_t)plan.tables * plan.vis_log_cap * 4;
   if (log_bytes > ix->vis_log.cap) {
     cudaError_t s = cudaStreamSynchronize(st);
     if (s != cudaSuccess) return cuda_error(s, "sync before scratch growth");
@@ -611,32 +623,54 @@ int ann_sync(ann_index* ix, void* stream, ann_search_stats* stats) {
   return collect(ix, static_cast<cudaStream_t>(stream), q, stats, false);
 }
 
-int ann_knn_exact(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
-                  int64_t nq, int32_t k, int32_t* ids, float* dists) {
+int ann_knn_exact_ex(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
+                     int64_t nq, int32_t k, int32_t engine, int32_t* ids, float* dists, float* kernel_ms) {
   if (!base || !queries || !ids || !dists) return set_error(ANN_EINVAL, "NULL buffer");
   if (dtype != ANN_U8 && dtype != ANN_F32) return set_error(ANN_EINVAL, "unknown dtype");
-  if (n < 1 || nq < 0 || k < 1 || k > 128 || d < 4 || d % 4 || d > (dtype == ANN_U8 ? 512 : 256))
+  if (n < 1 || n >= (1ll << 31) || nq < 0 || k < 1 || k > 128 || d < 4 || d % 4 ||
+      d > (dtype == ANN_U8 ? 512 : 256))
     return set_error(ANN_EINVAL, "knn: bad sizes (n=%lld d=%d k=%d)", (long long)n, d, k);
+  if (engine < ANN_KNN_AUTO || engine > ANN_KNN_CUDA_CORES)
+    return set_error(ANN_EINVAL, "knn: unknown engine %d", engine);
+  if (engine == ANN_KNN_TENSOR_CORES && (dtype != ANN_U8 || d > 128))
+    return set_error(ANN_EINVAL, "knn: the tensor-core engine needs uint8 data with d <= 128 (d=%d)", d);
+  if (kernel_ms) *kernel_ms = 0.f;
   if (nq == 0) return ANN_OK;
   const size_t es = elt_size(dtype);
   void *db = nullptr, *dq = nullptr;
   int32_t* di = nullptr;
   float* dd = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int timed_out = 0;
   cudaError_t e = cudaMalloc(&db, (size_t)n * d * es);
   if (e == cudaSuccess) e = cudaMalloc(&dq, (size_t)nq * d * es);
   if (e == cudaSuccess) e = cudaMalloc(&di, (size_t)nq * k * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dd, (size_t)nq * k * 4);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
   if (e == cudaSuccess) e = cudaMemcpy(db, base, (size_t)n * d * es, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dq, queries, (size_t)nq * d * es, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = knn_exact_device(db, dtype, n, d, dq, nq, k, di, dd, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ev0, 0);
+  if (e == cudaSuccess) e = knn_exact_device(db, dtype, n, d, dq, nq, k, di, dd, 0, engine, &timed_out);
+  if (e == cudaSuccess) e = cudaEventRecord(ev1, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+  if (e == cudaSuccess && kernel_ms) e = cudaEventElapsedTime(kernel_ms, ev0, ev1);
   if (e == cudaSuccess) e = cudaMemcpy(ids, di, (size_t)nq * k * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(dists, dd, (size_t)nq * k * 4, cudaMemcpyDeviceToHost);
   cudaFree(db);
   cudaFree(dq);
   cudaFree(di);
   cudaFree(dd);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   if (e != cudaSuccess) return cuda_error(e, "knn");
+  if (timed_out) return set_error(ANN_ETIMEOUT, "knn: a bounded wait of the tensor-core kernel ran out");
   return ANN_OK;
+}
+
+int ann_knn_exact(const void* base, int32_t dtype, int64_t n, int32_t d, const void* queries,
+                  int64_t nq, int32_t k, int32_t* ids, float* dists) {
+  return ann_knn_exact_ex(base, dtype, n, d, queries, nq, k, ANN_KNN_AUTO, ids, dists, nullptr);
 }
 
 int ann_probe_read_bandwidth(int64_t bytes, int32_t block_bytes, int32_t tier, int32_t iters,

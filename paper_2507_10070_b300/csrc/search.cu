@@ -953,6 +953,450 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
   }
 }
 
+// ---- Warp group per query (PQ navigation, uint8 data).
+//
+// W warps -- one block -- share one query's state in shared memory: its
+// lookup table (built W subspace pairs at a time), candidate list, results
+// and fetch ring, and one visited table.  Warp 0 keeps the pipeline exactly
+// as the warp-per-query kernel does (selection, fetch issue, the wait for its
+// own oldest fetch), so the schedule of fetches and expansions is the same.
+// Per expansion the other warps join in: each warp takes R/W of the node's
+// neighbour positions (visited set, code gathers, asymmetric distances), and
+// the merge of the step's new candidates into the list is split across the
+// warps.  Lists, steps and results therefore equal the warp-per-query
+// kernel's for every W; what changes is the time one step takes.
+struct WgCtl {
+  unsigned long long ukey;  // node expanded this step (its list key)
+  int act;                  // 1 = expand, 2 = stop
+  int slot;                 // ring slot holding its block
+  int len;                  // list length before this step's merge
+  int vis_count;            // visited-log entries of the query so far
+  int cand_count;           // candidates entering the list this step
+  int qi;                   // query the block works on
+};
+constexpr int kWgCtlBytes = 128;  // control words after the query's shared memory
+static_assert(sizeof(WgCtl) <= kWgCtlBytes, "control words");
+
+// Number of entries of sorted a[0..len) that are <= x.
+__device__ __forceinline__ int upper_bound_i32(const int* a, int len, int x) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <int NB, int W>
+__device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned char* ws,
+                             const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int warp,
+                             int lane, WgCtl* ctl) {
+  constexpr int kChunk = 32 * NB / W;                  // neighbour positions per warp
+  constexpr int NBW = kChunk >= 32 ? kChunk / 32 : 1;  // of them per lane
+  const long long t0 = global_timer_ns();
+  const int d = a.d, L = job.L, k = job.k, D = a.depth, n = a.n;
+  const int log2cap = a.vis_log2;
+  const unsigned cap_mask = (1u << log2cap) - 1u;
+  const int vis_limit = (3 << log2cap) >> 2;
+  const int tid = warp * 32 + lane;
+
+  unsigned* lut = reinterpret_cast<unsigned*>(ws + lay.lut);
+  unsigned char* ring = ws + lay.ring;
+  unsigned char* qs = ws + lay.q;
+  unsigned long long* res = reinterpret_cast<unsigned long long*>(ws + lay.res);
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(ws + lay.cand);
+  unsigned long long* ring_key = reinterpret_cast<unsigned long long*>(ws + lay.ring_key);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + lay.keys);
+  unsigned char* flags = ws + lay.flags;
+  int* rank = reinterpret_cast<int*>(ws + lay.rank);
+  const int slot_bytes = a.slot_bytes;
+
+  // ---- query vector into shared memory
+  {
+    const unsigned* src = static_cast<const unsigned*>(job.query);
+    unsigned* dst = reinterpret_cast<unsigned*>(qs);
+    for (int j = tid; j < (d >> 2); j += 32 * W) dst[j] = __ldg(src + j);
+  }
+  __syncthreads();
+
+  // ---- a1: lookup table, subspace pairs split across the warps
+  {
+    const int wps = a.dsub >> 2;
+    const unsigned* qw = reinterpret_cast<const unsigned*>(qs);
+    for (int m = 2 * warp; m < a.M; m += 2 * W) {
+      unsigned acc[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[h][j] = 0u;
+      for (int w = 0; w < wps; ++w) {
+        unsigned cv[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            cv[h][j] = __ldg(a.cb_words + (static_cast<size_t>(m + h) * 256 + lane + 32 * j) * wps + w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[h][j] = sq4(qw[(m + h) * wps + w], cv[h][j], acc[h][j]);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) lut[(m + h) * 256 + lane + 32 * j] = acc[h][j];
+    }
+  }
+  __syncthreads();
+
+  // ---- a2: entry node (warp 0)
+  int len = 1, nres = 0, head = 0, inflight = 0, steps = 0, status = ANN_OK, first_open = 0;
+  const int max_steps = n + 1;
+  if (warp == 0) {
+    const uint8_t* code = a.codes + static_cast<size_t>(a.entry) * a.M;
+    unsigned part = 0;
+    for (int m = lane; m < a.M; m += 32) part += lut[m * 256 + code[m]];
+    const unsigned entry_dist = warp_sum_u32(part);
+    if (lane == 0) {
+      keys[0] = make_key(entry_dist, a.entry);
+      flags[0] = 0;
+      const unsigned slot0 = hash_slot(a.entry, log2cap);
+      atomicCAS(vis + slot0, 0u, static_cast<unsigned>(a.entry) + 1u);
+      vlog[0] = slot0;
+      ctl->vis_count = 1;
+    }
+    for (int j = lane; j < k; j += 32) res[j] = kNoKey;
+    __syncwarp();
+  }
+
+  for (;;) {
+    // ---- a3-a5 (warp 0): select, issue fetches, and wait for the oldest
+    // when more than D are in flight or nothing is selectable
+    if (warp == 0) {
+      int act = 0, slot_u = 0;
+      unsigned long long ukey = 0;
+      do {
+        int sel = -1;
+        if (status == ANN_OK) {
+          for (int b = first_open; b < len; b += 32) {
+            const int i = b + lane;
+            const unsigned m = __ballot_sync(kFull, i < len && flags[i] == 0);
+            if (m) {
+              sel = b + __ffs(m) - 1;
+              break;
+            }
+          }
+          first_open = sel >= 0 ? sel + 1 : len;
+        }
+        if (sel >= 0) {
+          const unsigned long long key = keys[sel];
+          const unsigned v = static_cast<unsigned>(key);
+          int slot = head + inflight;
+          if (slot > D) slot -= D + 1;
+          __syncwarp();
+          if (lane == 0) {
+            flags[sel] = 1;
+            ring_key[slot] = key;
+          }
+          const uint8_t* src = a.blocks + static_cast<size_t>(v) * a.block_bytes;
+          unsigned char* dst = ring + slot * slot_bytes;
+          for (int off = lane * 16; off < slot_bytes; off += 512) cp_async_16(dst + off, src + off);
+          cp_async_commit();
+          ++inflight;
+          __syncwarp();
+        }
+        if (inflight > D || (sel < 0 && inflight > 0)) {
+          if (status != ANN_OK) {  // stopping early: drain, expand nothing more
+            cp_async_wait_pending(0);
+            __syncwarp();
+            inflight = 0;
+            act = 2;
+          } else {
+            cp_async_wait_pending(inflight - 1);
+            __syncwarp();
+            slot_u = head;
+            ukey = ring_key[head];
+            head = (head == D) ? 0 : head + 1;
+            --inflight;
+            ++steps;
+            act = 1;
+          }
+        } else if (sel < 0) {
+          act = 2;  // ---- a10: nothing selectable, nothing in flight
+        }
+      } while (act == 0);
+      if (lane == 0) {
+        ctl->act = act;
+        ctl->slot = slot_u;
+        ctl->ukey = ukey;
+        ctl->len = len;
+        ctl->cand_count = 0;
+      }
+    }
+    __syncthreads();  // the block landed (warp 0 waited for it); control published
+    if (ctl->act == 2) break;
+    const unsigned char* blk = ring + ctl->slot * slot_bytes;
+    const int lenv = ctl->len;
+    const unsigned long long thr = (lenv == L) ? keys[L - 1] : kNoKey;
+
+    // ---- a6 (warp 0): exact distance of the expanded node into the results
+    if (warp == 0) {
+      const unsigned* xw = reinterpret_cast<const unsigned*>(blk);
+      const unsigned* qw = reinterpret_cast<const unsigned*>(qs);
+      unsigned acc = 0;
+      for (int j = lane; j < (d >> 2); j += 32) acc = sq4(qw[j], xw[j], acc);
+      result_insert(res, nres, k, make_key(warp_sum_u32(acc), static_cast<unsigned>(ctl->ukey)), lane);
+    }
+
+    // ---- a7: this warp's neighbour positions and the visited set
+    const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + a.ids_off);
+    int w[NBW];
+    unsigned pos[NBW];
+    bool pending[NBW], fresh[NBW];
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      const int jj = t * 32 + lane;
+      const int j = warp * kChunk + jj;
+      int id = (jj < kChunk && j < a.R) ? nbr[j] : -1;
+      if (id >= n) id = -1;
+      w[t] = id;
+      pending[t] = id >= 0;
+      fresh[t] = false;
+      pos[t] = pending[t] ? hash_slot(static_cast<unsigned>(id), log2cap) : 0u;
+    }
+    uint4 code[NBW][kMaxM / 16];
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      if (w[t] >= 0) {
+        const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
+#pragma unroll
+        for (int c = 0; c < kMaxM / 16; ++c)
+          if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
+      }
+    }
+    unsigned old[NBW];
+#pragma unroll
+    for (int t = 0; t < NBW; ++t)
+      old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      if (pending[t]) {
+        if (old[t] == 0u) {
+          fresh[t] = true;
+          pending[t] = false;
+        } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
+          pending[t] = false;
+        } else {
+          pos[t] = (pos[t] + 1u) & cap_mask;
+        }
+      }
+    }
+    // ---- a8: asymmetric distances from the lookup table
+    unsigned long long key[NBW];
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      key[t] = kNoKey;
+      if (fresh[t] || pending[t]) {
+        unsigned dist = 0;
+#pragma unroll
+        for (int c = 0; c < kMaxM / 16; ++c) {
+          if (c < (a.M >> 4)) {
+            const unsigned wd[4] = {code[t][c].x, code[t][c].y, code[t][c].z, code[t][c].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int m0 = c * 16 + e * 4;
+              dist += lut[(m0 + 0) * 256 + (wd[e] & 0xff)];
+              dist += lut[(m0 + 1) * 256 + ((wd[e] >> 8) & 0xff)];
+              dist += lut[(m0 + 2) * 256 + ((wd[e] >> 16) & 0xff)];
+              dist += lut[(m0 + 3) * 256 + (wd[e] >> 24)];
+            }
+          }
+        }
+        key[t] = make_key(dist, static_cast<unsigned>(w[t]));
+      }
+    }
+    // a collided neighbour that could never enter the list is not probed
+    // further (its visited status cannot change any later step)
+#pragma unroll
+    for (int t = 0; t < NBW; ++t)
+      if (pending[t] && key[t] >= thr) pending[t] = false;
+    for (int probe = 0; probe < static_cast<int>(cap_mask); ++probe) {
+      bool any = false;
+#pragma unroll
+      for (int t = 0; t < NBW; ++t) any |= pending[t];
+      if (!__any_sync(kFull, any)) break;
+#pragma unroll
+      for (int t = 0; t < NBW; ++t)
+        old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
+#pragma unroll
+      for (int t = 0; t < NBW; ++t) {
+        if (pending[t]) {
+          if (old[t] == 0u) {
+            fresh[t] = true;
+            pending[t] = false;
+          } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
+            pending[t] = false;
+          } else {
+            pos[t] = (pos[t] + 1u) & cap_mask;
+          }
+        }
+      }
+    }
+    // fresh slots to the clear log, entering keys to the step's candidates
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      const unsigned mf = __ballot_sync(kFull, fresh[t]);
+      if (mf) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->vis_count, __popc(mf));
+        base = __shfl_sync(kFull, base, 0);
+        if (fresh[t]) vlog[base + __popc(mf & lt_mask)] = pos[t];
+      }
+      const bool enter = fresh[t] && key[t] < thr;
+      const unsigned me = __ballot_sync(kFull, enter);
+      if (me) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->cand_count, __popc(me));
+        base = __shfl_sync(kFull, base, 0);
+        if (enter) cand[base + __popc(me & lt_mask)] = key[t];
+      }
+    }
+    __syncthreads();  // every warp's candidates and log entries are in
+
+    // ---- a9: sort the candidates (warp 0), rank them in the list, move the
+    // list's tail right in rounds of W blocks (all reads of a round before
+    // its writes; entries only move right, so the rounds run top-down), then
+    // drop the candidates into their places; entries pushed past L fall off
+    const int c = ctl->cand_count;
+    if (c > 0) {
+      if (warp == 0) {
+        if (c <= 32) {
+          unsigned long long one[1] = {lane < c ? cand[lane] : kNoKey};
+          __syncwarp();
+          warp_bitonic_sort<1>(one, lane);
+          cand[lane] = one[0];
+        } else {
+          unsigned long long v[NB];
+#pragma unroll
+          for (int t = 0; t < NB; ++t) v[t] = (t * 32 + lane < c) ? cand[t * 32 + lane] : kNoKey;
+          __syncwarp();
+          warp_bitonic_sort<NB>(v, lane);
+#pragma unroll
+          for (int t = 0; t < NB; ++t) cand[t * 32 + lane] = v[t];
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < c; j += 32 * W) rank[j] = lower_bound_u64(keys, lenv, cand[j]);
+      __syncthreads();
+      const int pos0 = rank[0];
+      constexpr int kB = 256;  // entries per warp per round (8 per lane)
+      const int top_block = ((lenv - 1) / kB) * kB;
+      const int low_block = (pos0 / kB) * kB;
+      for (int r0 = top_block; r0 >= low_block; r0 -= W * kB) {
+        const int b = r0 - warp * kB;
+        unsigned long long kv[8];
+        unsigned char fv[8];
+        int np[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = b + t * 32 + lane;
+          const bool live = b >= low_block && i >= pos0 && i < lenv;
+          kv[t] = live ? keys[i] : 0ull;
+          fv[t] = live ? flags[i] : 0;
+          np[t] = !live ? L : (i >= rank[c - 1] ? i + c : i + upper_bound_i32(rank, c, i));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (np[t] < L) {
+            keys[np[t]] = kv[t];
+            flags[np[t]] = fv[t];
+          }
+        }
+        __syncthreads();
+      }
+      for (int j = tid; j < c; j += 32 * W) {
+        const int p = j + rank[j];
+        if (p < L) {
+          keys[p] = cand[j];
+          flags[p] = 0;
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        len = (lenv + c < L) ? lenv + c : L;
+        if (pos0 < first_open) first_open = pos0;
+      }
+    }
+    if (warp == 0 && (ctl->vis_count > vis_limit || steps >= max_steps)) status = ANN_ENOMEM;
+  }
+
+  // ---- a11: results (warp 0); the visited slots are cleared by every warp
+  if (warp == 0) {
+    for (int j = lane; j < k; j += 32) {
+      const unsigned long long r = j < nres ? res[j] : kNoKey;
+      const bool ok = r != kNoKey;
+      const int32_t id = static_cast<int32_t>(r & 0xffffffffu);
+      job.ids[j] = ok ? (a.id_map ? __ldg(a.id_map + id) : id) : -1;
+      job.dists[j] = ok ? static_cast<float>(static_cast<unsigned>(r >> 32)) : __int_as_float(0x7f800000);
+    }
+  }
+  const int visited = ctl->vis_count;
+  for (int j0 = warp * 256; j0 < visited; j0 += 256 * W) {
+    unsigned slot[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 32 * u + lane;
+      slot[u] = j < visited ? vlog[j] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (slot[u] != 0xffffffffu) vis[slot[u]] = 0u;
+  }
+  if (warp == 0 && lane == 0) {
+    if (job.steps) *job.steps = steps;
+    if (job.status) *job.status = status;
+    if (job.t_begin) *job.t_begin = t0;
+    if (job.t_end) *job.t_end = global_timer_ns();
+    atomicAdd(a.expansions, static_cast<unsigned long long>(steps));
+    if (status != ANN_OK) {
+      atomicAdd(&a.counters[1], 1);
+      atomicMin(&a.counters[2], job.qi);
+    }
+  }
+  __syncthreads();  // the table is clear and the control words free for the next query
+}
+
+// Persistent warp-group kernel: one query per block of W warps.
+template <int NB, int W>
+__global__ void __launch_bounds__(32 * W) search_kernel_wg(SearchArgs a, int smem_per_query) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WgCtl* ctl = reinterpret_cast<WgCtl*>(smem + smem_per_query);
+  const WarpSmem lay = warp_smem_layout(kModePqU8, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
+  uint32_t* vis = a.vis + (static_cast<size_t>(blockIdx.x) << a.vis_log2);
+  uint32_t* vlog = a.vis_log + static_cast<size_t>(blockIdx.x) * a.vis_log_cap;
+  for (;;) {
+    if (threadIdx.x == 0) ctl->qi = atomicAdd(&a.counters[0], 1);
+    __syncthreads();
+    const int qi = ctl->qi;
+    if (qi >= a.nq) break;
+    QueryJob job;
+    job.query = static_cast<const uint8_t*>(a.queries) + static_cast<size_t>(qi) * a.d;
+    job.k = a.k;
+    job.L = a.L;
+    job.qi = qi;
+    job.ids = a.ids + static_cast<size_t>(qi) * a.k;
+    job.dists = a.dists + static_cast<size_t>(qi) * a.k;
+    job.steps = a.steps ? a.steps + qi : nullptr;
+    job.status = a.status ? a.status + qi : nullptr;
+    job.t_begin = a.t_begin ? a.t_begin + qi : nullptr;
+    job.t_end = a.t_end ? a.t_end + qi : nullptr;
+    run_query_wg<NB, W>(a, job, smem, lay, vis, vlog, warp, lane, ctl);
+  }
+}
+
 __device__ __forceinline__ unsigned ld_relaxed_sys_u32(const void* p) {
   unsigned v;
   asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -1101,6 +1545,25 @@ cudaError_t launch_coop_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t
                                      static_cast<size_t>(smem), st);
 }
 
+template <int NB, int W>
+cudaError_t launch_wg_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) {
+  const int smem = p.smem_per_warp + kWgCtlBytes;
+  cudaError_t e = cudaFuncSetAttribute(search_kernel_wg<NB, W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  search_kernel_wg<NB, W><<<p.blocks, 32 * W, smem, st>>>(a, p.smem_per_warp);
+  return cudaGetLastError();
+}
+
+template <int NB, int W>
+cudaError_t occupancy_wg_t(int smem_block, int threads, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(search_kernel_wg<NB, W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel_wg<NB, W>,
+                                                       threads, smem_block);
+}
+
 template <int MODE, int NB>
 cudaError_t occupancy_t(int smem_block, int threads, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
@@ -1114,6 +1577,21 @@ using LaunchFn = cudaError_t (*)(const SearchArgs&, const SearchPlan&, cudaStrea
 using OccFn = cudaError_t (*)(int, int, int*);
 
 int nb_index(int nb) { return nb == 1 ? 0 : (nb == 2 ? 1 : 2); }
+
+// Warp-group kernels: [nb][W == 4]
+LaunchFn launch_wg_table(int nb, int w) {
+  static const LaunchFn t[3][2] = {{launch_wg_t<1, 2>, launch_wg_t<1, 4>},
+                                   {launch_wg_t<2, 2>, launch_wg_t<2, 4>},
+                                   {launch_wg_t<4, 2>, launch_wg_t<4, 4>}};
+  return t[nb_index(nb)][w == 4 ? 1 : 0];
+}
+
+OccFn occ_wg_table(int nb, int w) {
+  static const OccFn t[3][2] = {{occupancy_wg_t<1, 2>, occupancy_wg_t<1, 4>},
+                                {occupancy_wg_t<2, 2>, occupancy_wg_t<2, 4>},
+                                {occupancy_wg_t<4, 2>, occupancy_wg_t<4, 4>}};
+  return t[nb_index(nb)][w == 4 ? 1 : 0];
+}
 
 LaunchFn launch_table(int mode, int nb) {
   static const LaunchFn t[kNumModes][3] = {
@@ -1140,13 +1618,15 @@ OccFn occ_table(int mode, int nb) {
 }  // namespace
 
 cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth, int L, int k,
-                        int64_t nq, SearchPlan* plan) {
+                        int64_t nq, SearchPlan* plan, int64_t n_index, int wpq) {
   SearchPlan p;
   p.mode = mode;
   p.nb = R <= 32 ? 1 : (R <= 64 ? 2 : 4);
   const WarpSmem lay = warp_smem_layout(mode, M, d, slot_bytes, depth, L, k, p.nb);
   p.smem_per_warp = lay.total;
   p.warps_per_block = 1;
+  // a warp group per query: PQ navigation only; W warps share one query
+  p.wpq = (mode == kModePqU8 && (wpq == 2 || wpq == 4)) ? wpq : 1;
   // Visited table: 2^15 slots (2^16 beyond L = 2048), doubled for R > 64.
   // Measured on the 1M SIFT-like workload the largest visited set of 1,000
   // queries is ~12k nodes up to L = 2048 and ~18.5k at L = 4096 (R = 64), so
@@ -1154,8 +1634,18 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   // keeps the tables of the resident warps in L2.  Smaller degrees keep the
   // same size: at 10^7 nodes and R = 32 a query at L = 256 visited more than
   // the 12,288 nodes a halved table would hold.
-  int lg = L <= 2048 ? 15 : 16;
+  // Longer lists: 2^17 at L = 8192, 2^18 at L = 16384.  On indexes above
+  // 2^21 nodes a step finds more unseen neighbours (about 29 per step of
+  // R = 64 at 10^7 nodes, against about 9 at 10^6), so there the table holds
+  // 2 L R slots (3/4 of which may fill), up to 2^22.
+  int lg = L <= 2048 ? 15 : (L <= 4096 ? 16 : (L <= 8192 ? 17 : 18));
   if (R > 64) ++lg;
+  if (n_index > (int64_t(1) << 21)) {
+    int want = 0;
+    while ((int64_t(1) << want) < 2ll * L * R) ++want;
+    if (want > 22) want = 22;
+    if (want > lg) lg = want;
+  }
   p.vis_log2 = lg;
   p.vis_log_cap = (3 << lg) / 4 + 32 * p.nb + 1;
   int dev = 0, sms = 0, per_sm = 0;
@@ -1163,18 +1653,23 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = occ_table(mode, p.nb)(p.smem_per_warp * p.warps_per_block, 32 * p.warps_per_block, &per_sm);
+  if (p.wpq > 1)
+    e = occ_wg_table(p.nb, p.wpq)(p.smem_per_warp + kWgCtlBytes, 32 * p.wpq, &per_sm);
+  else
+    e = occ_table(mode, p.nb)(p.smem_per_warp * p.warps_per_block, 32 * p.warps_per_block, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t blocks = static_cast<int64_t>(sms) * per_sm;
-  const int64_t need = (nq + p.warps_per_block - 1) / p.warps_per_block;
+  const int64_t need = p.wpq > 1 ? nq : (nq + p.warps_per_block - 1) / p.warps_per_block;
   if (blocks > need) blocks = need > 0 ? need : 1;
   p.blocks = static_cast<int>(blocks);
+  p.tables = p.wpq > 1 ? p.blocks : p.blocks * p.warps_per_block;
   *plan = p;
   return cudaSuccess;
 }
 
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
+  if (plan.wpq > 1) return launch_wg_table(plan.nb, plan.wpq)(a, plan, stream);
   return launch_table(plan.mode, plan.nb)(a, plan, stream);
 }
 

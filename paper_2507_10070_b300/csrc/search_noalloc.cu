@@ -81,7 +81,7 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   if (rc != ANN_OK) return rc;
   if (nq == 0) return ANN_OK;
   SearchPlan plan;
-  cudaError_t e = plan_search(mode, a.R, a.M, a.d, slot_bytes, depth, L, k, nq, &plan);
+  cudaError_t e = plan_search(mode, a.R, a.M, a.d, slot_bytes, depth, L, k, nq, &plan, a.n);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
   const size_t table_bytes = (size_t(1) << plan.vis_log2) * 4;
   const size_t log_bytes = (size_t)plan.vis_log_cap * 4;
@@ -115,8 +115,13 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   a.t_end = trace ? trace->t_end : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The array keeps whatever the last call left: zero the counters and the
-  // visited tables this call uses (the kernel needs all-zero tables).
+  // visited tables this call uses (the kernel needs all-zero tables), then
+  // start counters[2] (lowest failed query, kept by atomicMin) at INT32_MAX,
+  // as the other entry points do.
+  static const int32_t kNoFailure = INT32_MAX;
   e = cudaMemsetAsync(sb, 0, kHeader, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sb + 2 * sizeof(int32_t), &kNoFailure, sizeof(kNoFailure),
+                                            cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.vis, 0, nwarps * table_bytes, st);
   if (e != cudaSuccess) return cuda_error(e, "clear static scratch");
   e = launch_search(a, plan, st);

@@ -87,12 +87,21 @@ void launcher_loop(ann_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->quit) {
-    if (s->running && cudaEventQuery(s->finished) == cudaSuccess) {
-      s->running = false;
-      unsigned long long h = 0;
-      if (cudaMemcpyAsync(&h, s->head_d, sizeof(h), cudaMemcpyDeviceToHost, s->stream) == cudaSuccess &&
-          cudaStreamSynchronize(s->stream) == cudaSuccess)
-        s->claimed = h;
+    if (s->running) {
+      // Any answer but "not ready" ends the run; an error (a failed kernel)
+      // is kept and returned by every later submit and poll.
+      const cudaError_t q = cudaEventQuery(s->finished);
+      if (q == cudaSuccess) {
+        s->running = false;
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, s->head_d, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) s->claimed = h;
+        else s->launch_error = e;
+      } else if (q != cudaErrorNotReady) {
+        s->running = false;
+        s->launch_error = q;
+      }
     }
     if (!s->running && s->published > s->claimed && s->launch_error == cudaSuccess) {
       cudaError_t e = launch_serve(s->args, s->sa, s->plan, s->stream);
@@ -165,7 +174,7 @@ int ann_serve_create(ann_index* ix, const ann_serve_cfg* cfg, ann_server** out) 
   }
   s->qbytes = s->args.d * (s->mode == kModeExactF32 ? 4 : 1);
   e = plan_search(s->mode, s->args.R, s->args.M, s->args.d, s->slot_bytes, cfg->depth,
-                  cfg->max_L, cfg->max_k, INT32_MAX, &s->plan);
+                  cfg->max_L, cfg->max_k, INT32_MAX, &s->plan, s->args.n);
   if (e != cudaSuccess) {
     delete s;
     return cuda_error(e, "plan serving kernel");
@@ -307,6 +316,10 @@ int ann_serve_poll(ann_server* s, uint64_t req_id, int32_t* ids, float* dists, i
   for (;;) {
     while (ready < r.nq && s->done[(r.first + ready) % s->cfg.slots] == r.first + ready + 1) ++ready;
     if (ready == r.nq) break;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->launch_error != cudaSuccess) return cuda_error(s->launch_error, "serving kernel");
+    }
     if (std::chrono::steady_clock::now() >= deadline)
       return set_error(ANN_ETIMEOUT, "request %llu: %lld of %lld queries done", (unsigned long long)req_id,
                        (long long)ready, (long long)r.nq);

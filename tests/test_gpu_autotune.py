@@ -23,3 +23,7 @@ def test_degree_selector_follows_its_rule():
     assert r["depth"] == int(np.argmax(r["qps_by_depth"])) and all(q > 0 for q in r["qps_by_depth"])
     # more neighbours per step cost more computation per step
     assert t[2]["t_compute_us"] > t[0]["t_compute_us"]
+    # warps per query: the fastest of 1, 2, 4 at the chosen degree and depth
+    wq = r["qps_by_warps_per_query"]
+    assert set(wq) == {"1", "2", "4"} and all(v > 0 for v in wq.values())
+    assert r["warps_per_query"] == int(max(wq, key=wq.get))

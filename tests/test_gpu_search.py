@@ -18,20 +18,6 @@ REL = 1e-5
 
 
 @pytest.fixture(scope="module")
-def u8_pq():
-    """SIFT-like uint8 index, 20,000 nodes, R=64, PQ M=32: oracle-built."""
-    mx = datagen.sift_like()
-    n, nq = 20_000, 333                        # nq: a ragged tail over the grid
-    base, q = mx.base(n), mx.queries(nq)
-    cb = oracle.pq_train(base[:5000], 32, datagen.kmeanspp_uniforms(mx.seed, 32), iters=8)
-    codes = oracle.pq_encode(base, cb)
-    entry = oracle.medoid(base)
-    adj = oracle.vamana(base, 64, 1.2, 96, entry, datagen.build_order(mx.seed, n),
-                        datagen.random_out_neighbours(mx.seed, n, 64))
-    return dict(base=base, q=q, cb=cb, codes=codes, entry=entry, adj=adj)
-
-
-@pytest.fixture(scope="module")
 def pq_index(u8_pq):
     w = u8_pq
     ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],

@@ -1,0 +1,140 @@
+"""A warp group per query (ann_set_warps_per_query): 2 or 4 warps share one
+query's lookup table, list, fetch ring and visited set; warp 0 keeps the
+relaxed pipeline and the warps split each expansion's neighbours and the list
+merge.  The schedule is the single warp's, so ids, distances and per-query
+step counts must equal the oracle's bit for bit, at every depth."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2507_10070_b300 as ann
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pq_index(u8_pq):
+    w = u8_pq
+    ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"],
+                   tier=ann.ANN_TIER_HOST_PINNED)
+    yield ix
+    ix.close()
+
+
+def _oracle(w, k, L, depth, q=None, adj=None, base=None, codes=None, entry=None):
+    return oracle.search(w["base"] if base is None else base, w["adj"] if adj is None else adj,
+                         w["entry"] if entry is None else entry, w["q"] if q is None else q, k, L, depth,
+                         codebook=w["cb"], codes=w["codes"] if codes is None else codes)
+
+
+@pytest.mark.parametrize("W", [2, 4])
+@pytest.mark.parametrize("L", [16, 64, 256])
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_warp_group_bit_exact(u8_pq, pq_index, W, L, depth):
+    pq_index.set_warps_per_query(W)
+    try:
+        ids, dists, stats, tr = pq_index.search(u8_pq["q"], 10, L, depth, trace=True)
+    finally:
+        pq_index.set_warps_per_query(1)
+    oi, od, osteps = _oracle(u8_pq, 10, L, depth)
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], osteps)
+    assert np.all(tr["status"] == 0) and stats.expansions == int(osteps.sum())
+
+
+@pytest.mark.parametrize("W", [2, 4])
+@pytest.mark.parametrize("k,L", [(1, 1), (33, 40), (256, 512), (10, 2048)])
+def test_warp_group_k_and_L_extremes(u8_pq, pq_index, W, k, L):
+    q = u8_pq["q"][:41]
+    pq_index.set_warps_per_query(W)
+    try:
+        ids, dists, _, tr = pq_index.search(q, k, L, 1, trace=True)
+    finally:
+        pq_index.set_warps_per_query(1)
+    oi, od, os_ = _oracle(u8_pq, k, L, 1, q=q)
+    assert np.array_equal(ids, oi) and np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
+@pytest.mark.parametrize("R", [32, 128])
+@pytest.mark.parametrize("W", [2, 4])
+def test_warp_group_degrees_and_repeated_ids(u8_pq, R, W):
+    """Random-link rows of 32 and 128 ids (one and four neighbour slots per
+    lane in the single-warp kernel), folded onto 500 ids so rows repeat ids
+    and link to themselves."""
+    w = u8_pq
+    n = 3000
+    base = w["base"][:n]
+    codes = np.ascontiguousarray(w["codes"][:n])
+    adj = datagen.random_links(2, n, R) % 500
+    ix = ann.Index(base, adj, 7, w["cb"], codes, tier=ann.ANN_TIER_HOST_PINNED)
+    try:
+        ix.set_warps_per_query(W)
+        ids, d, _, tr = ix.search(w["q"][:100], 10, 128, 1, trace=True)
+    finally:
+        ix.close()
+    oi, od, os_ = _oracle(w, 10, 128, 1, q=w["q"][:100], adj=adj, base=base, codes=codes, entry=7)
+    assert np.array_equal(ids, oi) and np.array_equal(d.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
+def test_warp_group_device_call_matches_host_call(u8_pq, pq_index):
+    import torch
+    q = torch.from_numpy(u8_pq["q"]).cuda()
+    nq = q.shape[0]
+    ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
+    d = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    pq_index.set_warps_per_query(4)
+    try:
+        pq_index.search_dev(q, 10, 128, 1, ids, d, stream=st)
+        stats = pq_index.sync(st)
+    finally:
+        pq_index.set_warps_per_query(1)
+    ref = pq_index.search(u8_pq["q"], 10, 128, 1)
+    assert np.array_equal(ids.cpu().numpy(), ref[0]) and np.array_equal(d.cpu().numpy(), ref[1])
+    assert stats.expansions == ref[2].expansions
+
+
+def test_warp_group_overflow_reports_enomem_and_recovers(u8_pq):
+    """A random-link graph of 60,000 nodes and R = 128 (random vectors and
+    codes) at L = 2048: a query visits more nodes than its visited table
+    takes (3/4 of 2^16 = 49,152), so it must report ANN_ENOMEM, for every
+    group size; the index then serves a normal search bit-exactly."""
+    w = u8_pq
+    n = 60_000
+    rng_base = datagen.random_bytes(3, n, 128)
+    cb = w["cb"]
+    codes = datagen.random_bytes(5, n, 32)
+    adj = datagen.random_links(4, n, 128)
+    ix = ann.Index(rng_base, adj, 0, cb, codes, tier=ann.ANN_TIER_HOST_PINNED)
+    try:
+        q = w["q"][:4]
+        for W in (1, 2, 4):
+            ix.set_warps_per_query(W)
+            _, _, stats, tr = ix.search(q, 10, 2048, 1, trace=True)
+            assert np.all(tr["status"] == ann._abi.ANN_ENOMEM), W
+            assert stats.n_failed == 4
+        ix.set_warps_per_query(4)
+        ids, d, _, tr = ix.search(q, 10, 64, 1, trace=True)
+        oi, od, os_ = oracle.search(rng_base, adj, 0, q, 10, 64, 1, codebook=cb, codes=codes)
+        assert np.array_equal(ids, oi) and np.array_equal(d.astype(np.float64), od)
+        assert np.array_equal(tr["steps"], os_)
+    finally:
+        ix.close()
+
+
+def test_set_warps_per_query_validates(u8_pq, pq_index):
+    with pytest.raises(ann.AnnError):
+        pq_index.set_warps_per_query(3)
+    base = np.zeros((8, 8), np.float32)
+    adj = np.array([[1], [2], [3], [4], [5], [6], [7], [0]], np.int32)
+    ix = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
+    try:
+        with pytest.raises(ann.AnnError):
+            ix.set_warps_per_query(2)       # exact navigation: one warp per query only
+        ix.set_warps_per_query(1)
+    finally:
+        ix.close()
