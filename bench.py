@@ -38,11 +38,12 @@ sys.path.insert(0, ROOT)
 import datagen  # noqa: E402
 
 DATA = os.path.join(ROOT, "_data")
-# ncu counters of the current search kernel on a 200k-node case, per
-# expansion (profiles/search_kernel_pq_sift200k_L256.md): PCIe read bytes
-# (the storage tier, which bounds the kernel) and DRAM read + write bytes.
+# ncu counters of the current search kernel at the benchmark's operating point
+# (1M SIFT-like index, L=1280, depth 1, 1,000 queries), per expansion
+# (profiles/search_kernel_pq_sift1m_L1280.md): PCIe read bytes (the storage
+# tier, which bounds the kernel) and DRAM read + write bytes.
 NCU_PCIE_BYTES_PER_EXPANSION = 420.0
-NCU_DRAM_BYTES_PER_EXPANSION = 513.0
+NCU_DRAM_BYTES_PER_EXPANSION = 556.0
 METRIC = "QPS at recall@10>=0.95 on 1 B300, relaxed vs sync search; p50/p99 latency"
 WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Vamana R=64, PQ M=32 in HBM, 512 B node blocks in host pinned memory, k=10"
 
@@ -194,6 +195,7 @@ def run_ours(args, rank: int, world: int):
     def one(L, depth, trace=None):
         ix.search_dev(qd, k, L, depth, ids, dists, stream=stream, trace=trace)
 
+
     # ---- operating point: smallest L with recall >= 0.95, fastest depth there
     sweep = []
     chosen_L = None
@@ -236,6 +238,15 @@ def run_ours(args, rank: int, world: int):
         per_depth[depth] = {"qps": nq / (np.median(ms) * 1e-3), "recall": round(r, 4),
                             "mean_steps": st.expansions / max(st.queries, 1)}
     best_depth = max((d for d in args.depths if d > 0), key=lambda d: per_depth[d]["qps"])
+    # warps per query at the operating point: the fastest of 1, 2, 4 (the
+    # relaxed and the synchronous timed runs both use it)
+    per_wpq = {}
+    for W in args.wpq:
+        ix.set_warps_per_query(W)
+        ms, _ = timed(chosen_L, best_depth, 3, 1)
+        per_wpq[W] = nq / (np.median(ms) * 1e-3)
+    best_wpq = max(per_wpq, key=per_wpq.get)
+    ix.set_warps_per_query(best_wpq)
     fetch_bytes = int(st.bytes_per_expansion)
     probe_gbps = ann.probe_read_bandwidth(1 << 30, fetch_bytes, ann.ANN_TIER_HOST_PINNED, 64)
     setup_s = time.time() - t_setup
@@ -329,10 +340,12 @@ def run_ours(args, rank: int, world: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded Gaussian mixture shaped like SIFT; index built in-run by the library's tooling)",
         "config": {"workload": WORKLOAD, "n": args.n, "nq": nq, "k": k, "L": chosen_L,
-                   "depth": best_depth, "R": 64, "M": 32, "block_bytes": ix.block_bytes,
-                   "fetch_bytes_per_expansion": int(st.bytes_per_expansion),
-                   "tier": "host_pinned", "l2": "flushed between timed steps (256 MB write)",
+                   "depth": best_depth, "R": 64, "M": 32, "builder": args.builder,
+                   "warps_per_query": best_wpq,
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world} (queries independent, no collective)"},
+        "layout": {"block_bytes": ix.block_bytes, "fetch_bytes_per_expansion": int(st.bytes_per_expansion),
+                   "tier": "host_pinned", "pq_codes": "HBM"},
         "recall_at_10": round(recall, 4), "recall_at_10_sync": round(recall_sync, 4),
         "sync": {"value": round(qps_sync, 1), "ms_per_step": round(float(np.mean(ms_sync)), 4),
                  "mean_steps": round(st_sync.expansions / max(st_sync.queries, 1), 2)},
@@ -349,6 +362,7 @@ def run_ours(args, rank: int, world: int):
         "latency_us": {"p50": round(float(np.percentile(lat_us, 50)), 1),
                        "p99": round(float(np.percentile(lat_us, 99)), 1),
                        "what": "per-query device time from warp start to finish, in a full batch"},
+        "warps_per_query_qps": {str(W): round(v, 1) for W, v in per_wpq.items()},
         "sweep": {"recall_by_L_depth0": sweep,
                   "by_depth_at_L": {str(d): {kk: (round(v, 2) if isinstance(v, float) else v)
                                              for kk, v in per_depth[d].items()} for d in per_depth}},
@@ -376,9 +390,13 @@ def run_ours(args, rank: int, world: int):
         out["autotune"]["what"] = ("computation / I/O balanced degree selector on random-link "
                                    "100k-node sample indices (ann_autotune_degree)")
     if args.serve_seconds > 0:
-        out["serving"] = run_serving(ix, w, gt_ids, gt_d, chosen_L, best_depth, args.serve_seconds)
+        out["serving"] = run_serving(ix, w, gt_ids, gt_d, chosen_L, best_depth, args.serve_seconds,
+                                     probe_gbps=probe_gbps, fetch_bytes=fetch_bytes)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, chosen_L, args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(w, chosen_L, args.cpu_sample, best_depth)
+    if args.serving_workload and rank == 0:
+        ix.close()
+        out["serving_workload_1e7"] = run_serving_workload(args)
     if rank == 0:
         out["clocks"] = clk.summary()
     ix.close()
@@ -386,7 +404,7 @@ def run_ours(args, rank: int, world: int):
 
 
 def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
-                load: float = 0.7, seed: int = 7, Ls=None):
+                load: float = 0.7, seed: int = 7, Ls=None, probe_gbps=None, fetch_bytes=384):
     """Continuous-batching request loop.  Requests are batches of queries with
     size log-uniform in [1, 512], k in {10, 100} and L in {L*, 1.25 L*, 1.5 L*}
     (L* = the batch operating point).  Phase 1 keeps the server saturated to
@@ -408,12 +426,14 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
 
     srv = ann.Server(ix, max_L=max(Ls), max_k=100, depth=depth, slots=16384, idle_exit_us=100_000)
     hits = [0.0, 0]
+    expansions = [0]
 
     def collect(meta, on_done):
         for rid in srv.ready(0):
             ids, d, info = srv.poll(rid, 0)
             j = meta.pop(rid)
             on_done(j)
+            expansions[0] += int(info.expansions)
             s0, n = starts[j], sizes[j]
             hits[0] += ann.recall_at_k(ids[:, :10], gt_ids[s0:s0 + n], gt_d[s0:s0 + n], d[:, :10]) * n
             hits[1] += n
@@ -437,10 +457,12 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
             collect(meta, lambda j: done_q.__setitem__(0, done_q[0] + sizes[j]))
             time.sleep(2e-4)
         t_sat = time.perf_counter() - t0
+        exp_sat = expansions[0]
         while meta:
             collect(meta, lambda j: None)
             time.sleep(2e-4)
         capacity = done_q[0] / t_sat
+        sat_gbs = exp_sat * fetch_bytes / t_sat / 1e9
         # phase 2: Poisson arrivals at `load` x capacity
         mean_batch = 511.0 / np.log(512.0)
         rate = load * capacity / mean_batch
@@ -450,6 +472,7 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
         lat = []
         meta, i = {}, 0
         hits[0], hits[1] = 0.0, 0
+        expansions[0] = 0
         t0 = time.perf_counter()
         while i < n_req or meta:
             now = time.perf_counter() - t0
@@ -478,7 +501,17 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
             "recall_at_10": round(hits[0] / max(hits[1], 1), 4), "L_choices": Ls,
             "k_choices": [10, 100], "batch_size": "log-uniform [1, 512]",
             "kernel_launches": int(st.launches), "resident_warps": int(st.resident_warps),
-            "seconds": round(wall, 2)}
+            "seconds": round(wall, 2),
+            "roofline": {"bound": "pcie", "unit": "GB/s",
+                         "achieved_saturated": round(sat_gbs, 2),
+                         "achieved_at_load": round(expansions[0] * fetch_bytes / wall / 1e9, 2),
+                         "peak": None if probe_gbps is None else round(probe_gbps, 2),
+                         "frac_saturated": None if probe_gbps is None else round(sat_gbs / probe_gbps, 4),
+                         "expansions_saturated": int(exp_sat),
+                         "what": (f"storage-tier bytes the serving kernel read: expansions of the completed "
+                                  f"requests x {fetch_bytes} B (vector + neighbour ids) over wall time, "
+                                  "against the in-run random-read probe; the saturated phase keeps every "
+                                  "warp busy, the loaded phase runs at the offered load")}}
 
 
 def run_precision(args):
@@ -552,6 +585,45 @@ def run_precision(args):
                          "max_rel_dist_error_vs_fp64": float(f"{err:.3g}")})
         ix.close()
         out["variants"][name] = rows
+
+    # Where is the accuracy lost: navigation or the rerank budget?  At L=512,
+    # the rerank depth grows from 4k to 32k expanded candidates; for FP8 the
+    # encoding scale varies too.  A variant whose recall rises with the
+    # rerank depth was short of budget; one that stays put lost the true
+    # neighbours during navigation (they were never expanded).
+    def recall_at(ix, L):
+        ix.search_dev(qd, k, L, 1, ids, dists, stream=st)
+        ix.sync(st)
+        return round(ann.recall_at_k(ids.cpu().numpy(), gi, gd, dists.cpu().numpy()), 4)
+
+    Lr = max(args.precision_Ls)
+    sweep = {"L": Lr, "by_rerank_mult": {}, "fp8_scale": {}}
+    for name, kw in (("bf16", dict(nav=ann.ANN_NAV_BF16)), ("fp8_e4m3", dict(nav=ann.ANN_NAV_FP8, nav_scale=64.0)),
+                     ("pq48", dict(codebook=cb, codes=codes))):
+        row = {}
+        for mult in (4, 8, 16, 32):
+            if "codebook" in kw:
+                ix = ann.Index(base, adj, entry, cb, codes, tier=ann.ANN_TIER_HBM, rerank_mult=mult)
+            else:
+                ix = ann.Index(base, adj, entry, tier=ann.ANN_TIER_HBM, rerank_mult=mult, **kw)
+            row[str(mult * k)] = recall_at(ix, Lr)
+            ix.close()
+        sweep["by_rerank_mult"][name] = row
+    for scale in (16.0, 64.0, 256.0):
+        ix = ann.Index(base, adj, entry, tier=ann.ANN_TIER_HBM, nav=ann.ANN_NAV_FP8, nav_scale=scale,
+                       rerank_mult=32)
+        sweep["fp8_scale"][str(scale)] = recall_at(ix, Lr)
+        ix.close()
+    # the candidates' own ceiling: recall if every expanded node were ranked
+    # exactly (navigation on each variant, rerank of all expanded nodes up to
+    # the 512 limit) is the 32k row; the FP32 traversal at the same L is the
+    # reference
+    ix = ann.Index(base, adj, entry, tier=ann.ANN_TIER_HBM)
+    sweep["fp32_traversal"] = recall_at(ix, Lr)
+    ix.close()
+    sweep["what"] = ("recall@10 at L = %d against the rerank depth (candidates reranked exactly in FP32) "
+                     "and, for FP8-E4M3, the encoding scale (rerank depth 320)" % Lr)
+    out["accuracy_loss"] = sweep
     return out
 
 
@@ -699,92 +771,134 @@ def run_large(args):
 def run_serving_workload(args):
     """Serving workload: 10^7 SIFT-like uint8 vectors (the 1M workload's
     generator: 256 centres, sigma 20), 10,000 queries.  The degree selector
-    picks R among {32, 48, 64, 96} and the pipeline depth; Vamana at that R
-    is built on the GPU and stored breadth-first, with the node blocks in
-    host pinned memory and 32-byte PQ codes in HBM.  Requests arrive as a
-    seeded Poisson stream of batches (size log-uniform in [1, 512], k in
-    {10, 100}, L in {64, 128, 256}; L raised to k where k > L) at 70% of the
-    measured capacity; the batched QPS and recall at each (L, k) are
-    reported beside it."""
+    picks R among {32, 48, 64, 96} (the GPU builder takes R <= 64), the
+    pipeline depth and the warps per query on random-link samples; Vamana at
+    that R is built on the GPU and stored breadth-first, with the node blocks
+    in host pinned memory and 32-byte PQ codes in HBM.  The operating point
+    is the smallest L of the sweep whose recall@10 reaches 0.95; there the
+    batched search is timed synchronously (depth 0) and relaxed, at 1, 2 and
+    4 warps per query.  The serving loop then takes a seeded Poisson stream
+    of request batches (size log-uniform in [1, 512], k in {10, 100}) at 70%
+    of its measured capacity, twice: with L in {L*, 1.25 L*, 1.5 L*} (the
+    operating point) and with the prescribed L in {64, 128, 256}."""
     import torch
     import paper_2507_10070_b300 as ann
     torch.cuda.set_device(0)
     n, nq, M = args.serving_n, 10_000, 32
     t0 = time.time()
-    at = ann.autotune_degree(degrees=(32, 48, 64, 96), n_sample=100_000, d=128, M=M, L=32, nq=4096, seed=1)
-    R, depth = min(at["degree"], 64), at["depth"]
+    at = ann.autotune_degree(degrees=(32, 48, 64, 96), n_sample=100_000, d=128, M=M, L=256, nq=2048, seed=1)
+    R = min(at["degree"], 64)
     mx = datagen.sift_like()
     base, q = mx.base(n), mx.queries(nq)
     cb, codes = ann.build_pq(base, M, n_train=100_000, iters=25,
                              kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, M), encode_device="gpu")
     adj, entry = ann.build_graph(base, R, 1.2, 128, seed=mx.seed, device="gpu")
-    gt_ids, gt_d = ann.knn_exact(base, q, 100)
+    gt_ids, gt_d, gt_ms = ann.knn_exact(base, q, 100, return_ms=True)
     b2, a2, e2, c2, old = ann.reorder_graph(base, adj, entry, codes)
     del adj, codes
     ix = ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
     setup = time.time() - t0
     qd = torch.from_numpy(q).cuda()
     st = torch.cuda.Stream()
-    batch = {}
-    for L0 in (64, 128, 256):
-        for k in (10, 100):
-            L = max(L0, k)
-            ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
-            dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
-            ix.search_dev(qd, k, L, depth, ids, dists, stream=st)
-            ix.sync(st)
+    ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
+    dists = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    depth_t = max(at["depth"], 1)   # the relaxed run; depth 0 is the synchronous baseline
+
+    def timed(L, depth, reps=2):
+        ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
+        ix.sync(st)
+        ms = []
+        for _ in range(reps):
+            with torch.cuda.stream(st):
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            for _ in range(3):
-                ix.search_dev(qd, k, L, depth, ids, dists, stream=st)
+            ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
             e1.record(st)
-            ix.sync(st)
+            s = ix.sync(st)
             torch.cuda.synchronize()
-            r = ann.recall_at_k(ids.cpu().numpy()[:, :10], gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy()[:, :10])
-            batch[f"L{L0}_k{k}"] = {"L_searched": L, "qps": round(3 * nq / (e0.elapsed_time(e1) * 1e-3), 1),
-                                   "recall_at_10": round(r, 4)}
+            ms.append(e0.elapsed_time(e1))
+        m = float(np.median(ms))
+        r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
+        return {"qps": round(nq / (m * 1e-3), 1), "recall_at_10": round(r, 4),
+                "mean_steps": round(s.expansions / max(s.queries, 1), 1),
+                "pcie_gbs": round(s.expansions * s.bytes_per_expansion / (m * 1e-3) / 1e9, 2)}
+
+    curve, L_star = [], None
+    for L in (128, 256, 512, 1024, 2048, 4096, 8192, 16384):
+        ix.search_dev(qd, 10, L, depth_t, ids, dists, stream=st)
+        ix.sync(st)
+        r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
+        curve.append({"L": L, "recall_at_10": round(r, 4)})
+        if r >= 0.95:
+            L_star = L
+            break
+    op = {"L": L_star}
+    if L_star is not None:
+        by_w = {}
+        for W in (1, 2, 4):
+            ix.set_warps_per_query(W)
+            by_w[str(W)] = timed(L_star, depth_t)
+        best_w = int(max(by_w, key=lambda x: by_w[x]["qps"]))
+        ix.set_warps_per_query(best_w)
+        op.update(depth=depth_t, warps_per_query=best_w, relaxed=by_w[str(best_w)],
+                  sync=timed(L_star, 0), by_warps_per_query=by_w)
+        op["relaxed_over_sync"] = round(op["relaxed"]["qps"] / op["sync"]["qps"], 4)
+        probe = ann.probe_read_bandwidth(1 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
+        op["roofline"] = {"bound": "pcie", "achieved": op["relaxed"]["pcie_gbs"], "peak": round(probe, 2),
+                          "unit": "GB/s", "frac": round(op["relaxed"]["pcie_gbs"] / probe, 4)}
     with ClockSampler(0) as clk:
-        serving = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], 128, depth,
-                              args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=(64, 128, 256))
+        Ls_op = None if L_star is None else (L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32)
+        serving_op = None
+        if Ls_op is not None:
+            serving_op = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], L_star, depth_t,
+                                     args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=Ls_op,
+                                     probe_gbps=op["roofline"]["peak"])
+        serving_spec = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], 128, depth_t,
+                                   args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=(64, 128, 256))
     ix.close()
     return {"what": run_serving_workload.__doc__.split("\n\n")[0].replace("\n", " "),
-            "n": n, "nq": nq, "M": M, "R": R, "depth": depth, "autotune": at,
-            "batched": batch, "serving": serving, "clocks": clk.summary(),
-            "setup_s": round(setup, 1)}
+            "n": n, "nq": nq, "M": M, "R": R, "autotune": at, "recall_curve": curve,
+            "operating_point": op, "serving_at_operating_point": serving_op,
+            "serving_prescribed_L": serving_spec, "clocks": clk.summary(),
+            "ground_truth_ms": round(gt_ms, 1), "setup_s": round(setup, 1)}
 
 
-def cpu_baseline(w, L: int, sample: int):
-    """The CPU oracle as it stands (synchronous search, every host core) on the
-    first `sample` queries of the same workload and index."""
+def cpu_baseline(w, L: int, sample: int, depth: int = 0):
+    """The CPU oracle as it stands (every host core, the relaxed schedule at
+    `depth`) on the first `sample` queries of the same workload and index."""
     import oracle
     threads = oracle.default_threads()
     q = w["q"][:sample]
-    oracle.search(w["base"], w["adj"], w["entry"], q[: min(64, sample)], 10, L, 0,
+    oracle.search(w["base"], w["adj"], w["entry"], q[: min(64, sample)], 10, L, depth,
                   codebook=w["cb"], codes=w["codes"], threads=threads)
     t0 = time.perf_counter()
-    oracle.search(w["base"], w["adj"], w["entry"], q, 10, L, 0, codebook=w["cb"], codes=w["codes"],
+    oracle.search(w["base"], w["adj"], w["entry"], q, 10, L, depth, codebook=w["cb"], codes=w["codes"],
                   threads=threads)
     dt = time.perf_counter() - t0
     return {"value": round(len(q) / dt, 1), "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": (f"all {len(q):,} queries" if len(q) == w["q"].shape[0] else
-                       f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f", L={L}, depth 0, k=10"}
+                       f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f", L={L}, depth {depth}, k=10"}
 
 
 def run_reference(args):
-    """The oracle arm: each step searches a bounded sample of the queries on
-    the host cores (synchronous best-first search).  Its index (same workload,
-    R, PQ and build parameters) is built by the library's host tooling, so no
-    CUDA code runs on this arm.  L is chosen by the GPU arm's rule (smallest L
-    with recall@10 >= 0.95), judged on the first 200 queries against the
-    oracle's own brute-force ground truth."""
+    """The oracle arm: each step searches the queries on the host cores with
+    the relaxed schedule at depth `--ref-depth` (1, the paper's default
+    staleness and the GPU arm's usual choice).  Its index is the GPU arm's
+    default one (same workload, R, PQ and build parameters, built by the
+    library's host tooling, so no CUDA code runs on this arm).  L is chosen by
+    the GPU arm's rule (smallest L with recall@10 >= 0.95), judged on the
+    first 200 queries against the oracle's own brute-force ground truth."""
     import oracle
     w = prepare_sift_like(args.n, args.nq, builder="cpu")
     threads = oracle.default_threads()
     qs = w["q"][:200]
     gi, gd = oracle.knn(w["base"], qs, 10, threads)
     L = args.Ls[-1]
+    depth = args.ref_depth
     for Lc in args.Ls:
-        ids, d, _ = oracle.search(w["base"], w["adj"], w["entry"], qs, 10, Lc, 0, codebook=w["cb"],
+        ids, d, _ = oracle.search(w["base"], w["adj"], w["entry"], qs, 10, Lc, depth, codebook=w["cb"],
                                   codes=w["codes"], threads=threads)
         if oracle.recall_at_k(ids, gi, gd, d) >= args.target_recall:
             L = Lc
@@ -793,23 +907,124 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.search(w["base"], w["adj"], w["entry"], q, 10, L, 0, codebook=w["cb"],
+        oracle.search(w["base"], w["adj"], w["entry"], q, 10, L, depth, codebook=w["cb"],
                       codes=w["codes"], threads=threads)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     qps = len(q) * args.steps / sum(times)
     sample = (f"all {len(q):,} queries" if len(q) == w["q"].shape[0] else
-              f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f" per step, L={L}, depth 0, k=10"
+              f"first {len(q):,} of the {w['q'].shape[0]:,} queries") + f" per step, L={L}, depth {depth}, k=10"
     return {"impl": "reference", "metric": METRIC, "value": round(qps, 1), "unit": "queries/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(times) / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "nq": len(q), "k": 10, "L": L,
-                       "depth": 0},
+                       "depth": depth, "R": 64, "M": 32, "builder": "cpu",
+                       "note": ("same index as the GPU arm's default (host-built graph and PQ); L by the "
+                                "same recall rule on a 200-query sample; the GPU arm picks its depth by "
+                                "speed among 1, 2, 4 (1 in practice)")},
             "cpu_baseline": {"value": round(qps, 1), "unit": "queries/s", "cores": threads,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(qps, 1), "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+def run_kernel_case(args):
+    """One small, fixed invocation of one kernel family, for ncu captures
+    (each case keeps a few GB on the device and launches its kernel a few
+    times; the profile summaries under profiles/ name the case they used).
+
+    search  the search kernel on the 1M SIFT-like index (node blocks in host
+            pinned memory): --case-nq queries at --case-L / --case-depth,
+            --case-wpq warps per query, 3 launches
+    serve   the serving kernel on the same index: --case-nq queries in
+            requests of 100 at --case-L, k=10, depth --case-depth
+    nav     FP32 / BF16 / FP8-E4M3 navigation and the FP32 rerank on 10^6
+            DEEP-like float32 vectors (graph R=48 built on the GPU), vectors
+            in HBM, --case-nq queries at --case-L, 2 launches each
+    knn     brute-force ground truth: 10^6 SIFT-like vectors x --case-nq
+            queries, tensor-core engine then CUDA-core engine, k=10
+    build   index tooling: GPU PQ encoding and Vamana on the GPU (R=64,
+            L_build=128) over 200,000 SIFT-like vectors"""
+    import torch
+    import paper_2507_10070_b300 as ann
+    torch.cuda.set_device(0)
+    case, nq, L, depth = args.kernel_case, args.case_nq, args.case_L, args.case_depth
+    out = {"kernel_case": case, "nq": nq, "L": L, "depth": depth}
+    st = torch.cuda.Stream()
+    if case in ("search", "serve"):
+        w = prepare_sift_like(args.n, args.nq, builder=args.builder)
+        ix = ann.Index(w["base"], w["adj"], w["entry"], w["cb"], w["codes"], tier=ann.ANN_TIER_HOST_PINNED)
+        q = w["q"][:nq]
+        if case == "search":
+            ix.set_warps_per_query(args.case_wpq)
+            qd = torch.from_numpy(q).cuda()
+            ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
+            dists = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+            ms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
+                e1.record(st)
+                s = ix.sync(st)
+                torch.cuda.synchronize()
+                ms.append(round(e0.elapsed_time(e1), 3))
+            out.update(ms=ms, expansions_per_launch=int(s.expansions), wpq=args.case_wpq,
+                       bytes_per_expansion=int(s.bytes_per_expansion))
+        else:
+            srv = ann.Server(ix, max_L=L, max_k=10, depth=depth, slots=16384, idle_exit_us=20_000)
+            try:
+                t0 = time.perf_counter()
+                rids = [srv.submit(q[i:i + 100], 10, L) for i in range(0, nq, 100)]
+                exp = 0
+                for rid in rids:
+                    r = None
+                    while r is None:
+                        r = srv.poll(rid, 100_000)
+                    exp += int(r[2].expansions)
+                out.update(seconds=round(time.perf_counter() - t0, 3), expansions=exp,
+                           launches=int(srv.stats().launches))
+            finally:
+                srv.close()
+        ix.close()
+    elif case == "nav":
+        mx = datagen.deep_like()
+        base, q = mx.base(1_000_000), mx.queries(nq)
+        adj, entry = ann.build_graph(base, 48, 1.2, 96, seed=mx.seed, device="gpu")
+        qd = torch.from_numpy(q).cuda()
+        ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
+        dists = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+        for name, kw in (("fp32", {}), ("bf16", dict(nav=ann.ANN_NAV_BF16)),
+                         ("fp8_e4m3", dict(nav=ann.ANN_NAV_FP8, nav_scale=64.0))):
+            ix = ann.Index(base, adj, entry, tier=ann.ANN_TIER_HBM, **kw)
+            ms = []
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
+                e1.record(st)
+                s = ix.sync(st)
+                torch.cuda.synchronize()
+                ms.append(round(e0.elapsed_time(e1), 3))
+            out[name] = {"ms": ms, "expansions": int(s.expansions)}
+            ix.close()
+    elif case == "knn":
+        mx = datagen.sift_like()
+        base, q = mx.base(1_000_000), mx.queries(nq)
+        for eng in ("tensor", "cuda"):
+            _, _, ms = ann.knn_exact(base, q, 10, engine=eng, return_ms=True)
+            out[eng] = {"ms": round(ms, 3), "tflops": round(2e6 * nq * 128 / (ms * 1e-3) / 1e12, 2)}
+    elif case == "build":
+        mx = datagen.sift_like()
+        base = mx.base(200_000)
+        t0 = time.time()
+        cb, codes = ann.build_pq(base, 32, n_train=20_000, iters=5,
+                                 kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, 32), encode_device="gpu")
+        t1 = time.time()
+        ann.build_graph(base, 64, 1.2, 128, seed=mx.seed, device="gpu")
+        out.update(pq_s=round(t1 - t0, 2), graph_s=round(time.time() - t1, 2))
+    return out
 
 
 def main():
@@ -826,13 +1041,15 @@ def main():
     ap.add_argument("--target-recall", type=float, default=0.95)
     ap.add_argument("--cpu-sample", type=int, default=10_000,
                     help="queries the CPU oracle searches (per step on the reference arm)")
-    ap.add_argument("--ref-L", type=int, default=256)
+    ap.add_argument("--ref-depth", type=int, default=1,
+                    help="relaxed-pipeline depth of the oracle arm's search")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="length of the serving (request loop) measurement; 0 skips it")
     ap.add_argument("--autotune", type=int, default=1, help="run the degree selector (1) or not (0)")
-    ap.add_argument("--builder", choices=["cpu", "gpu"], default="gpu",
-                    help="Vamana construction for the index (off the clock)")
+    ap.add_argument("--builder", choices=["cpu", "gpu"], default="cpu",
+                    help="Vamana construction for the index (off the clock); the host-built "
+                         "index is the one the full-size parity test searches with the oracle")
     ap.add_argument("--precision", action="store_true",
                     help="only run the precision workload (float32 DEEP-like, BF16/FP8/PQ navigation)")
     ap.add_argument("--precision-n", type=int, default=10_000_000)
@@ -840,6 +1057,10 @@ def main():
     ap.add_argument("--serving", action="store_true",
                     help="only run the serving workload (10^7 uint8 vectors, autotuned R and depth)")
     ap.add_argument("--serving-n", type=int, default=10_000_000)
+    ap.add_argument("--serving-workload", type=int, default=1,
+                    help="also run the 10^7 serving workload after the headline (1) or not (0)")
+    ap.add_argument("--wpq", type=int, nargs="+", default=[1, 2, 4],
+                    help="warps per query tried at the operating point")
     ap.add_argument("--large", action="store_true",
                     help="only run the large out-of-core workload (10^8 uint8 vectors by default)")
     ap.add_argument("--large-n", type=int, default=100_000_000)
@@ -847,6 +1068,12 @@ def main():
     ap.add_argument("--large-Lb", type=int, default=128, help="L_build of the large index")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only print the storage-tier probe's GB/s for several read sizes")
+    ap.add_argument("--kernel-case", choices=["search", "serve", "nav", "knn", "build"],
+                    help="only run one small, fixed invocation of a kernel family (for ncu captures)")
+    ap.add_argument("--case-nq", type=int, default=1000)
+    ap.add_argument("--case-L", type=int, default=1280)
+    ap.add_argument("--case-depth", type=int, default=1)
+    ap.add_argument("--case-wpq", type=int, default=1)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -858,6 +1085,9 @@ def main():
         return
     if args.serving:
         print(json.dumps(run_serving_workload(args)), flush=True)
+        return
+    if args.kernel_case:
+        print(json.dumps(run_kernel_case(args)), flush=True)
         return
     if args.probe_sweep:
         import paper_2507_10070_b300 as ann
