@@ -427,13 +427,15 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
     srv = ann.Server(ix, max_L=max(Ls), max_k=100, depth=depth, slots=16384, idle_exit_us=100_000)
     hits = [0.0, 0]
     expansions = [0]
+    overflows = [0]
 
     def collect(meta, on_done):
         for rid in srv.ready(0):
-            ids, d, info = srv.poll(rid, 0)
+            ids, d, info = srv.poll(rid, 0, check=False)
             j = meta.pop(rid)
             on_done(j)
             expansions[0] += int(info.expansions)
+            overflows[0] += int(info.n_failed)
             s0, n = starts[j], sizes[j]
             hits[0] += ann.recall_at_k(ids[:, :10], gt_ids[s0:s0 + n], gt_d[s0:s0 + n], d[:, :10]) * n
             hits[1] += n
@@ -501,7 +503,7 @@ def run_serving(ix, w, gt_ids, gt_d, L_star: int, depth: int, seconds: float,
             "recall_at_10": round(hits[0] / max(hits[1], 1), 4), "L_choices": Ls,
             "k_choices": [10, 100], "batch_size": "log-uniform [1, 512]",
             "kernel_launches": int(st.launches), "resident_warps": int(st.resident_warps),
-            "seconds": round(wall, 2),
+            "seconds": round(wall, 2), "visited_overflow_queries": int(overflows[0]),
             "roofline": {"bound": "pcie", "unit": "GB/s",
                          "achieved_saturated": round(sat_gbs, 2),
                          "achieved_at_load": round(expansions[0] * fetch_bytes / wall / 1e9, 2),
@@ -807,7 +809,7 @@ def run_serving_workload(args):
 
     def timed(L, depth, reps=2):
         ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
-        ix.sync(st)
+        ix.sync(st, check=False)
         ms = []
         for _ in range(reps):
             with torch.cuda.stream(st):
@@ -816,21 +818,22 @@ def run_serving_workload(args):
             e0.record(st)
             ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
             e1.record(st)
-            s = ix.sync(st)
+            s = ix.sync(st, check=False)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         m = float(np.median(ms))
         r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
         return {"qps": round(nq / (m * 1e-3), 1), "recall_at_10": round(r, 4),
+                "visited_overflows": int(s.n_failed),
                 "mean_steps": round(s.expansions / max(s.queries, 1), 1),
                 "pcie_gbs": round(s.expansions * s.bytes_per_expansion / (m * 1e-3) / 1e9, 2)}
 
     curve, L_star = [], None
     for L in (128, 256, 512, 1024, 2048, 4096, 8192, 16384):
         ix.search_dev(qd, 10, L, depth_t, ids, dists, stream=st)
-        ix.sync(st)
+        s = ix.sync(st, check=False)
         r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
-        curve.append({"L": L, "recall_at_10": round(r, 4)})
+        curve.append({"L": L, "recall_at_10": round(r, 4), "visited_overflows": int(s.n_failed)})
         if r >= 0.95:
             L_star = L
             break
@@ -991,7 +994,16 @@ def run_kernel_case(args):
     elif case == "nav":
         mx = datagen.deep_like()
         base, q = mx.base(1_000_000), mx.queries(nq)
-        adj, entry = ann.build_graph(base, 48, 1.2, 96, seed=mx.seed, device="gpu")
+        os.makedirs(DATA, exist_ok=True)
+        path = os.path.join(DATA, "deep_like_n1000000_R48_gpu.npz")
+        if os.path.exists(path):   # cached, so a profiled rerun launches no build kernels
+            z = np.load(path)
+            adj, entry = z["adj"], int(z["entry"])
+        else:
+            adj, entry = ann.build_graph(base, 48, 1.2, 96, seed=mx.seed, device="gpu")
+            tmp = path + f".{os.getpid()}.tmp.npz"
+            np.savez(tmp, adj=adj, entry=entry)
+            os.replace(tmp, path)
         qd = torch.from_numpy(q).cuda()
         ids = torch.empty((nq, 10), dtype=torch.int32, device="cuda")
         dists = torch.empty((nq, 10), dtype=torch.float32, device="cuda")

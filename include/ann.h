@@ -235,7 +235,7 @@ int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
  *    visited table and clear log need more than 16 MiB / 32 = 512 KiB per
  *    warp is rejected with ANN_EINVAL (on indexes up to 2^21 nodes: R > 64
  *    with L > 2048, or L > 4096; on larger indexes the table grows with
- *    L * R, so L * R > 2^15 is rejected).  At most 16 MiB / (per-warp
+ *    L * R, so L * R > 2^14 is rejected).  At most 16 MiB / (per-warp
  *    scratch) warps run, fewer than ann_search_dev may use, so throughput
  *    is lower.
  *  - The first call on each device looks up the array's device address

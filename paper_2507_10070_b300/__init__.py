@@ -192,10 +192,15 @@ class Index:
                                              ctypes.c_void_p(dists.data_ptr()),
                                              ctypes.byref(tr) if tr else None, st))
 
-    def sync(self, stream=None) -> SearchStats:
+    def sync(self, stream=None, check: bool = True) -> SearchStats:
+        """Wait for the stream; totals of the device calls since the last sync.
+        With check=False a visited-set overflow (ANN_ENOMEM) does not raise:
+        stats.n_failed says how many queries it stopped."""
         stats = SearchStats()
         st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
-        _check(_lib().ann_sync(self._h, st, ctypes.byref(stats)))
+        rc = _lib().ann_sync(self._h, st, ctypes.byref(stats))
+        if rc != 0 and not (rc == _abi.ANN_ENOMEM and not check):
+            _check(rc)
         return stats
 
 
@@ -220,8 +225,10 @@ class Server:
         self._k[rid.value] = (q.shape[0], k)
         return rid.value
 
-    def poll(self, req_id: int, timeout_us: int = 0):
-        """(ids, dists, info) once the request is done, or None if not yet."""
+    def poll(self, req_id: int, timeout_us: int = 0, check: bool = True):
+        """(ids, dists, info) once the request is done, or None if not yet.
+        With check=False a visited-set overflow (ANN_ENOMEM) does not raise:
+        info.n_failed counts the queries it stopped."""
         nq, k = self._k[req_id]
         ids = np.empty((nq, k), np.int32)
         dists = np.empty((nq, k), np.float32)
@@ -231,7 +238,8 @@ class Server:
         if rc == _abi.ANN_ETIMEOUT:
             return None
         del self._k[req_id]
-        _check(rc)
+        if not (rc == _abi.ANN_ENOMEM and not check):
+            _check(rc)
         return ids, dists, info
 
     def ready(self, timeout_us: int = 0, max_n: int = 4096):

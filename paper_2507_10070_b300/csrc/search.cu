@@ -1636,13 +1636,14 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   // the 12,288 nodes a halved table would hold.
   // Longer lists: 2^17 at L = 8192, 2^18 at L = 16384.  On indexes above
   // 2^21 nodes a step finds more unseen neighbours (about 29 per step of
-  // R = 64 at 10^7 nodes, against about 9 at 10^6), so there the table holds
-  // 2 L R slots (3/4 of which may fill), up to 2^22.
+  // R = 64 at 10^7 nodes, against about 9 at 10^6; a query takes about
+  // 1.6 L steps), so a query visits about 0.7 L R nodes there, twice that in
+  // the tail: the table holds 4 L R slots (3/4 of which may fill), up to 2^22.
   int lg = L <= 2048 ? 15 : (L <= 4096 ? 16 : (L <= 8192 ? 17 : 18));
   if (R > 64) ++lg;
   if (n_index > (int64_t(1) << 21)) {
     int want = 0;
-    while ((int64_t(1) << want) < 2ll * L * R) ++want;
+    while ((int64_t(1) << want) < 4ll * L * R) ++want;
     if (want > 22) want = 22;
     if (want > lg) lg = want;
   }

@@ -149,7 +149,7 @@ def test_edge_cases(u8_pq, pq_index):
     oi, od, _ = _oracle_pq(u8_pq, 5, 5, 4, q=u8_pq["q"][:1])
     assert np.array_equal(ids, oi)
     # argument errors
-    for k, L, depth in [(0, 10, 0), (11, 10, 0), (10, 4097, 0), (10, 32, 5), (10, 32, -1)]:
+    for k, L, depth in [(0, 10, 0), (11, 10, 0), (10, 16385, 0), (10, 32, 5), (10, 32, -1)]:
         with pytest.raises(ann.AnnError):
             pq_index.search(u8_pq["q"][:4], k, L, depth)
 
