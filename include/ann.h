@@ -35,7 +35,7 @@ extern "C" {
 typedef enum {
   ANN_OK = 0,
   ANN_EINVAL = -1,   /* bad argument or malformed index data */
-  ANN_ENOMEM = -2,   /* allocation failed, or a query overflowed its visited set */
+  ANN_ENOMEM = -2,   /* allocation failed */
   ANN_ECUDA = -3,    /* a CUDA runtime call failed */
   ANN_ETIMEOUT = -4, /* a bounded device-side wait ran out */
   ANN_EBUSY = -5,    /* the index is in use by another search */
@@ -104,8 +104,7 @@ typedef struct {
  * ann_search_dev). */
 typedef struct {
   int32_t* steps;   /* [nq] node blocks fetched and expanded (search steps) */
-  int32_t* status;  /* [nq] ANN_OK, ANN_ENOMEM if the visited set overflowed, or
-                       ANN_ETIMEOUT (kernel-grained ablation only) */
+  int32_t* status;  /* [nq] ANN_OK, or ANN_ETIMEOUT (kernel-grained ablation only) */
   int64_t* t_begin; /* [nq] device global timer (ns) when the query started */
   int64_t* t_end;   /* [nq] device global timer (ns) when it finished */
 } ann_trace;
@@ -180,8 +179,8 @@ int ann_set_warps_per_query(ann_index* index, int32_t warps);
  *    fewer than k nodes were expanded.
  *  trace: host pointers, may be NULL.  stats: may be NULL.
  * Blocks until done.  One search at a time per index (ANN_EBUSY otherwise).
- * Returns ANN_ENOMEM if any query overflowed its visited set (that query's
- * status says so and its results are what it had found).
+ * Each resident query keeps its visited set as one bit per node of the index
+ * (n/8 bytes of device scratch per resident query), so it cannot overflow.
  */
 int ann_search(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
                int32_t depth, int32_t* ids, float* dists, const ann_trace* trace,
@@ -227,17 +226,15 @@ int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);
  * synchronise the device), a process whose device memory is reserved up
  * front by its own pool, or code that must not grow its footprint after
  * start-up.  The search is the same kernel and gives the same results; its
- * scratch (visited tables, their clear logs, counters) lives in one 16 MiB
+ * scratch (visited bitsets, their clear logs, counters) lives in one 16 MiB
  * device array inside the library, which every GPU that loads the library
  * holds until the process exits.  The caller still passes queries and outputs
  * (device memory, as for ann_search_dev) and loads the index beforehand.
- *  - Limit: a call must fit the scratch of at least 32 warps; a call whose
- *    visited table and clear log need more than 16 MiB / 32 = 512 KiB per
- *    warp is rejected with ANN_EINVAL (on indexes up to 2^21 nodes: R > 64
- *    with L > 2048, or L > 4096; on larger indexes the table grows with
- *    L * R, so L * R > 2^14 is rejected).  At most 16 MiB / (per-warp
- *    scratch) warps run, fewer than ann_search_dev may use, so throughput
- *    is lower.
+ *  - Limit: a call must fit the scratch of at least 32 warps.  A warp
+ *    needs one bit per node of the index (rounded up to 128 bytes) and a
+ *    32 KiB clear log, so indexes above 3,931,136 nodes are rejected with
+ *    ANN_EINVAL.  At most 16 MiB / (per-warp scratch) warps run, fewer than
+ *    ann_search_dev may use, so throughput is lower.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress with that device current).  With CUDA's lazy
  *    module loading (the default) that lookup is also what loads the
@@ -287,7 +284,7 @@ typedef struct {
 typedef struct {
   int64_t queries;     /* queries of the request */
   int64_t expansions;  /* node blocks fetched for them */
-  int32_t n_failed;    /* queries that overflowed their visited set */
+  int32_t n_failed;    /* queries whose status is not ANN_OK */
   int64_t device_ns;   /* device time from the first query's start to the last one's end */
 } ann_serve_result;
 
@@ -312,8 +309,7 @@ int ann_serve_submit(ann_server* server, const void* queries, int64_t nq, int32_
 /* Wait up to timeout_us (0: just check) for a request.  On completion copies
  * its nq*k ids and dists to host memory (same layout as ann_search), fills
  * `info` (may be NULL), frees its slots and forgets the request; returns
- * ANN_ETIMEOUT if it is not done yet (call again), ANN_ENOMEM if a query
- * overflowed its visited set (results copied all the same). */
+ * ANN_ETIMEOUT if it is not done yet (call again). */
 int ann_serve_poll(ann_server* server, uint64_t req_id, int32_t* ids, float* dists,
                    int64_t timeout_us, ann_serve_result* info);
 

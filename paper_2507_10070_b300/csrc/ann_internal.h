@@ -33,6 +33,7 @@ constexpr int kMaxDepth = 4;
 constexpr int kMaxR = 128;
 constexpr int kMaxD = 512;
 constexpr int kMaxM = 64;
+constexpr int kVisLog = 8192;  // entries of a query's visited-set clear log
 
 // Everything one launch of the search kernel reads or writes.
 struct SearchArgs {
@@ -63,10 +64,10 @@ struct SearchArgs {
   int64_t* t_begin;
   int64_t* t_end;
   // scratch
-  uint32_t* vis;            // per-warp open-addressing visited tables, all zero between queries
-  int32_t vis_log2;         // log2 of the table capacity per warp
-  uint32_t* vis_log;        // per-warp log of the table slots a query used (to clear them)
-  int32_t vis_log_cap;      // entries per warp in vis_log
+  uint32_t* vis;            // per-query visited bitsets (one bit per node), all zero between queries
+  int64_t vis_words;        // 32-bit words per bitset (a multiple of 32)
+  uint32_t* vis_log;        // per-bitset log of the words a query set (to clear them)
+  int32_t vis_log_cap;      // entries per bitset in vis_log
   int32_t* counters;        // [0] next query, [1] failed queries, [2] first failed query
   unsigned long long* expansions;  // running total of expansions
 };
@@ -101,7 +102,7 @@ struct SearchPlan {
   int wpq;             // warps per query: 1, or 2 / 4 (one query per block, PQ mode)
   int blocks;          // grid size (persistent)
   int tables;          // visited tables (and clear logs) the launch uses
-  int vis_log2;
+  int64_t vis_words;   // words per visited bitset
   int vis_log_cap;
 };
 

@@ -339,7 +339,7 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   const int mode = dtype == ANN_U8 ? kModeExactU8 : kModeExactF32;
   const int pool = std::min(L_build + 64, kCandMax - R);  // results kept per search
   SearchPlan plan;
-  cudaError_t e = plan_search(mode, R, 0, d, stride * 4, 0, L_build, pool, max_batch, &plan);
+  cudaError_t e = plan_search(mode, R, 0, d, stride * 4, 0, L_build, pool, max_batch, &plan, n);
   if (e != cudaSuccess) return cuda_error(e, "plan build search");
   const size_t nwarps = (size_t)plan.blocks * plan.warps_per_block;
   uint8_t *base_d = nullptr, *qbuf = nullptr;
@@ -402,8 +402,8 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   GB_TRY(dmalloc(&qbuf, (size_t)max_batch * row_bytes), "cudaMalloc batch");
   GB_TRY(dmalloc(&cand_ids, (size_t)max_batch * pool), "cudaMalloc candidates");
   GB_TRY(dmalloc(&cand_d, (size_t)max_batch * pool), "cudaMalloc candidates");
-  GB_TRY(dmalloc(&vis, nwarps << plan.vis_log2), "cudaMalloc visited");
-  GB_TRY(cudaMemset(vis, 0, (nwarps << plan.vis_log2) * 4), "cudaMemset");
+  GB_TRY(dmalloc(&vis, nwarps * plan.vis_words), "cudaMalloc visited");
+  GB_TRY(cudaMemset(vis, 0, nwarps * plan.vis_words * 4), "cudaMemset");
   GB_TRY(dmalloc(&vlog, nwarps * plan.vis_log_cap), "cudaMalloc visited log");
   GB_TRY(dmalloc(&counters, 4), "cudaMalloc counters");
   GB_TRY(dmalloc(&exp_d, 1), "cudaMalloc counters");
@@ -443,7 +443,7 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   a.ids = cand_ids;
   a.dists = cand_d;
   a.vis = vis;
-  a.vis_log2 = plan.vis_log2;
+  a.vis_words = plan.vis_words;
   a.vis_log = vlog;
   a.vis_log_cap = plan.vis_log_cap;
   a.counters = counters;

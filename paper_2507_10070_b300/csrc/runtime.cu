@@ -404,7 +404,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan, ix->n,
                               kernel_grained ? 1 : ix->wpq);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
-  const size_t want = ((size_t)plan.tables) << plan.vis_log2;
+  const size_t want = (size_t)plan.tables * (size_t)plan.vis_words;
   if (want > ix->vis_words) {
     // tables must start all-zero; the kernel clears after each query
     cudaError_t s = cudaStreamSynchronize(st);
@@ -473,7 +473,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   a.t_begin = tr ? tr->t_begin : nullptr;
   a.t_end = tr ? tr->t_end : nullptr;
   a.vis = ix->vis;
-  a.vis_log2 = plan.vis_log2;
+  a.vis_words = plan.vis_words;
   a.vis_log = static_cast<uint32_t*>(ix->vis_log.p);
   a.vis_log_cap = plan.vis_log_cap;
   a.counters = ix->counters;
@@ -518,7 +518,7 @@ int collect(ann_index* ix, cudaStream_t st, int64_t queries, ann_search_stats* s
   if (c[3] != 0)
     return set_error(ANN_ETIMEOUT, "a kernel-grained round barrier timed out (%d queries failed)", c[1]);
   if (c[1] > 0)
-    return set_error(ANN_ENOMEM, "%d queries overflowed their visited set (first: query %d)", c[1], c[2]);
+    return set_error(ANN_ENOMEM, "%d queries stopped early (first: query %d)", c[1], c[2]);
   return ANN_OK;
 }
 

@@ -196,8 +196,29 @@ __device__ bool grid_round(unsigned* bar, int* timed_out, int lane, int* all_don
   return __shfl_sync(kFull, ok, 0) != 0;
 }
 
-__device__ __forceinline__ unsigned hash_slot(unsigned id, int log2cap) {
-  return (id * 2654435761u) >> (32 - log2cap);
+// Empty a query's visited bitset after the query: through the log of the
+// words it set while the log held them all and that is the smaller job,
+// otherwise every word.  `part` of `parts` warps takes its share.
+__device__ __forceinline__ void clear_visited(uint32_t* vis, const uint32_t* vlog, int visited,
+                                              int log_cap, int64_t words, int lane, int part,
+                                              int parts) {
+  if (visited <= log_cap && static_cast<int64_t>(visited) * 8 <= words) {
+    // eight log entries per lane in flight: the log is read back from L2
+    for (int j0 = part * 256; j0 < visited; j0 += 256 * parts) {
+      unsigned wd[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + 32 * u + lane;
+        wd[u] = j < visited ? vlog[j] : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (wd[u] != 0xffffffffu) vis[wd[u]] = 0u;
+    }
+  } else {
+    uint4* v4 = reinterpret_cast<uint4*>(vis);  // words is a multiple of 32
+    for (int64_t j = part * 32 + lane; j < (words >> 2); j += 32 * parts) v4[j] = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 struct QueryState {
@@ -451,9 +472,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
                           const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int lane) {
   const long long t0 = global_timer_ns();
   const int d = a.d, L = job.L, k = job.k, D = a.depth, n = a.n;
-  const int log2cap = a.vis_log2;
-  const unsigned cap_mask = (1u << log2cap) - 1u;
-  const int vis_limit = (3 << log2cap) >> 2;  // overflow above 3/4 load
+  const int log_cap = a.vis_log_cap;
 
   unsigned* lut = reinterpret_cast<unsigned*>(ws + lay.lut);
   unsigned char* ring = ws + lay.ring;
@@ -556,9 +575,8 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   if (lane == 0) {
     s.keys[0] = make_key(entry_dist, a.entry);
     s.flags[0] = 0;
-    const unsigned slot0 = hash_slot(a.entry, log2cap);
-    atomicCAS(vis + slot0, 0u, static_cast<unsigned>(a.entry) + 1u);
-    vlog[0] = slot0;
+    atomicOr(vis + (static_cast<unsigned>(a.entry) >> 5), 1u << (a.entry & 31));
+    vlog[0] = static_cast<unsigned>(a.entry) >> 5;
   }
   for (int j = lane; j < k; j += 32) res[j] = kNoKey;
   __syncwarp();
@@ -638,17 +656,15 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       const int deg = a.R;
       const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + (MODE == kModePqU8 ? a.ids_off : 0));
       int w[NB];
-      unsigned pos[NB];
-      bool pending[NB], fresh[NB];
+      unsigned word[NB];
+      bool fresh[NB];
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const int j = t * 32 + lane;
         int id = j < deg ? nbr[j] : -1;
         if (id >= n) id = -1;  // validated at load; never trusted blindly
         w[t] = id;
-        pending[t] = id >= 0;
-        fresh[t] = false;
-        pos[t] = pending[t] ? hash_slot(static_cast<unsigned>(id), log2cap) : 0u;
+        word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
       }
       // PQ codes of every listed neighbour, issued before the visited probes
       // so that both round trips overlap.
@@ -664,33 +680,23 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
           }
         }
       }
-      // Visited set, first round: one CAS on every neighbour's home slot, in
-      // flight together with the code loads above.
+      // Visited set: one atomicOr per neighbour on its bit, in flight
+      // together with the code loads above; the neighbour is new if its bit
+      // was clear (a repeated id in the row finds it set by the first).
       unsigned old[NB];
 #pragma unroll
       for (int t = 0; t < NB; ++t)
-        old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
+        old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
 #pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        if (pending[t]) {
-          if (old[t] == 0u) {
-            fresh[t] = true;
-            pending[t] = false;
-          } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
-            pending[t] = false;  // seen before
-          } else {
-            pos[t] = (pos[t] + 1u) & cap_mask;  // collided: decided below
-          }
-        }
-      }
+      for (int t = 0; t < NB; ++t) fresh[t] = w[t] >= 0 && ((old[t] >> (w[t] & 31)) & 1u) == 0u;
 
-      // ---- a8: navigation distances of the neighbours not known to be seen
+      // ---- a8: navigation distances of the new neighbours
       unsigned long long key[NB];
       if (MODE == kModePqF32) {
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
-          if (fresh[t] || pending[t]) {
+          if (fresh[t]) {
             float dist = 0.f;
 #pragma unroll
             for (int c = 0; c < kMaxM / 16; ++c) {
@@ -713,7 +719,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
-          if (fresh[t] || pending[t]) {
+          if (fresh[t]) {
             unsigned dist = 0;
 #pragma unroll
             for (int c = 0; c < kMaxM / 16; ++c) {
@@ -746,7 +752,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           key[t] = kNoKey;
-          unsigned m = __ballot_sync(kFull, fresh[t] || pending[t]);
+          unsigned m = __ballot_sync(kFull, fresh[t]);
           while (m) {
             // group g evaluates the neighbour held by the g-th set lane of m
             unsigned mm = m;
@@ -772,47 +778,21 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
         }
       }
 
-      // A key at or above the L-th entry of a full list can never enter: the
-      // L-th key only decreases while the list stays full, and navigation
-      // distances are fixed per query.  Such a node's visited status cannot
-      // change any later step, so a collided one is not probed further.
+      // A key at or above the L-th entry of a full list cannot enter it.
       const unsigned long long thr = (s.len == L) ? s.keys[L - 1] : kNoKey;
-#pragma unroll
-      for (int t = 0; t < NB; ++t)
-        if (pending[t] && key[t] >= thr) pending[t] = false;
-      for (int probe = 0; probe < static_cast<int>(cap_mask); ++probe) {
-        bool any = false;
-#pragma unroll
-        for (int t = 0; t < NB; ++t) any |= pending[t];
-        if (!__any_sync(kFull, any)) break;
-#pragma unroll
-        for (int t = 0; t < NB; ++t)
-          old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          if (pending[t]) {
-            if (old[t] == 0u) {
-              fresh[t] = true;
-              pending[t] = false;
-            } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
-              pending[t] = false;
-            } else {
-              pos[t] = (pos[t] + 1u) & cap_mask;
-            }
-          }
-        }
-      }
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (!fresh[t]) key[t] = kNoKey;
 
-      // append the newly used slots to this warp's clear log
+      // log the words of the new nodes' bits (while the log has room), so
+      // the clear after the query touches only those
       int nfresh = 0;
       const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const unsigned m = __ballot_sync(kFull, fresh[t]);
-        if (fresh[t]) vlog[visited + nfresh + __popc(m & lt_mask)] = pos[t];
+        const int at = visited + nfresh + __popc(m & lt_mask);
+        if (fresh[t] && at < log_cap) vlog[at] = word[t];
         nfresh += __popc(m);
       }
       visited += nfresh;
@@ -856,7 +836,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       }
       __syncwarp();
 
-      if (visited > vis_limit || steps >= max_steps) {
+      if (steps >= max_steps) {  // cannot happen: each node is expanded at most once
         status = ANN_ENOMEM;
         break;
       }
@@ -878,21 +858,10 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
     job.dists[j] = ok ? (mode_f32(MODE) ? __uint_as_float(dbits) : static_cast<float>(dbits))
                       : __int_as_float(0x7f800000);
   }
-  // Clear the slots this query used, so the table is all zero for the next
-  // query of this warp.
+  // Clear the bits this query set, so the set is empty for the next query
+  // of this warp.
   __syncwarp();
-  // (eight log entries per lane in flight: the log is read back from L2)
-  for (int j0 = 0; j0 < visited; j0 += 256) {
-    unsigned slot[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int j = j0 + 32 * u + lane;
-      slot[u] = j < visited ? vlog[j] : 0xffffffffu;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (slot[u] != 0xffffffffu) vis[slot[u]] = 0u;
-  }
+  clear_visited(vis, vlog, visited, log_cap, a.vis_words, lane, 0, 1);
   if (lane == 0) {
     if (job.steps) *job.steps = steps;
     if (job.status) *job.status = status;
@@ -916,7 +885,7 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
   unsigned char* ws = smem + wib * smem_per_warp;
   const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
   const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
-  uint32_t* vis = a.vis + (gw << a.vis_log2);
+  uint32_t* vis = a.vis + gw * static_cast<size_t>(a.vis_words);
   uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
   for (;;) {
     if (a.grid_bar && ld_acquire_gpu_u32(reinterpret_cast<const unsigned*>(a.counters + 3))) break;
@@ -995,9 +964,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
   constexpr int NBW = kChunk >= 32 ? kChunk / 32 : 1;  // of them per lane
   const long long t0 = global_timer_ns();
   const int d = a.d, L = job.L, k = job.k, D = a.depth, n = a.n;
-  const int log2cap = a.vis_log2;
-  const unsigned cap_mask = (1u << log2cap) - 1u;
-  const int vis_limit = (3 << log2cap) >> 2;
+  const int log_cap = a.vis_log_cap;
   const int tid = warp * 32 + lane;
 
   unsigned* lut = reinterpret_cast<unsigned*>(ws + lay.lut);
@@ -1060,9 +1027,8 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     if (lane == 0) {
       keys[0] = make_key(entry_dist, a.entry);
       flags[0] = 0;
-      const unsigned slot0 = hash_slot(a.entry, log2cap);
-      atomicCAS(vis + slot0, 0u, static_cast<unsigned>(a.entry) + 1u);
-      vlog[0] = slot0;
+      atomicOr(vis + (static_cast<unsigned>(a.entry) >> 5), 1u << (a.entry & 31));
+      vlog[0] = static_cast<unsigned>(a.entry) >> 5;
       ctl->vis_count = 1;
     }
     for (int j = lane; j < k; j += 32) res[j] = kNoKey;
@@ -1151,8 +1117,8 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     // ---- a7: this warp's neighbour positions and the visited set
     const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + a.ids_off);
     int w[NBW];
-    unsigned pos[NBW];
-    bool pending[NBW], fresh[NBW];
+    unsigned word[NBW];
+    bool fresh[NBW];
 #pragma unroll
     for (int t = 0; t < NBW; ++t) {
       const int jj = t * 32 + lane;
@@ -1160,9 +1126,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       int id = (jj < kChunk && j < a.R) ? nbr[j] : -1;
       if (id >= n) id = -1;
       w[t] = id;
-      pending[t] = id >= 0;
-      fresh[t] = false;
-      pos[t] = pending[t] ? hash_slot(static_cast<unsigned>(id), log2cap) : 0u;
+      word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
     }
     uint4 code[NBW][kMaxM / 16];
 #pragma unroll
@@ -1177,26 +1141,15 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     unsigned old[NBW];
 #pragma unroll
     for (int t = 0; t < NBW; ++t)
-      old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
+      old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
 #pragma unroll
-    for (int t = 0; t < NBW; ++t) {
-      if (pending[t]) {
-        if (old[t] == 0u) {
-          fresh[t] = true;
-          pending[t] = false;
-        } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
-          pending[t] = false;
-        } else {
-          pos[t] = (pos[t] + 1u) & cap_mask;
-        }
-      }
-    }
+    for (int t = 0; t < NBW; ++t) fresh[t] = w[t] >= 0 && ((old[t] >> (w[t] & 31)) & 1u) == 0u;
     // ---- a8: asymmetric distances from the lookup table
     unsigned long long key[NBW];
 #pragma unroll
     for (int t = 0; t < NBW; ++t) {
       key[t] = kNoKey;
-      if (fresh[t] || pending[t]) {
+      if (fresh[t]) {
         unsigned dist = 0;
 #pragma unroll
         for (int c = 0; c < kMaxM / 16; ++c) {
@@ -1215,34 +1168,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
         key[t] = make_key(dist, static_cast<unsigned>(w[t]));
       }
     }
-    // a collided neighbour that could never enter the list is not probed
-    // further (its visited status cannot change any later step)
-#pragma unroll
-    for (int t = 0; t < NBW; ++t)
-      if (pending[t] && key[t] >= thr) pending[t] = false;
-    for (int probe = 0; probe < static_cast<int>(cap_mask); ++probe) {
-      bool any = false;
-#pragma unroll
-      for (int t = 0; t < NBW; ++t) any |= pending[t];
-      if (!__any_sync(kFull, any)) break;
-#pragma unroll
-      for (int t = 0; t < NBW; ++t)
-        old[t] = pending[t] ? atomicCAS(vis + pos[t], 0u, static_cast<unsigned>(w[t]) + 1u) : 0u;
-#pragma unroll
-      for (int t = 0; t < NBW; ++t) {
-        if (pending[t]) {
-          if (old[t] == 0u) {
-            fresh[t] = true;
-            pending[t] = false;
-          } else if (old[t] == static_cast<unsigned>(w[t]) + 1u) {
-            pending[t] = false;
-          } else {
-            pos[t] = (pos[t] + 1u) & cap_mask;
-          }
-        }
-      }
-    }
-    // fresh slots to the clear log, entering keys to the step's candidates
+    // new nodes' words to the clear log, entering keys to the step's candidates
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int t = 0; t < NBW; ++t) {
@@ -1251,7 +1177,8 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
         int base = 0;
         if (lane == 0) base = atomicAdd(&ctl->vis_count, __popc(mf));
         base = __shfl_sync(kFull, base, 0);
-        if (fresh[t]) vlog[base + __popc(mf & lt_mask)] = pos[t];
+        const int at = base + __popc(mf & lt_mask);
+        if (fresh[t] && at < log_cap) vlog[at] = word[t];
       }
       const bool enter = fresh[t] && key[t] < thr;
       const unsigned me = __ballot_sync(kFull, enter);
@@ -1329,7 +1256,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
         if (pos0 < first_open) first_open = pos0;
       }
     }
-    if (warp == 0 && (ctl->vis_count > vis_limit || steps >= max_steps)) status = ANN_ENOMEM;
+    if (warp == 0 && steps >= max_steps) status = ANN_ENOMEM;  // cannot happen (each node expands once)
   }
 
   // ---- a11: results (warp 0); the visited slots are cleared by every warp
@@ -1342,18 +1269,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       job.dists[j] = ok ? static_cast<float>(static_cast<unsigned>(r >> 32)) : __int_as_float(0x7f800000);
     }
   }
-  const int visited = ctl->vis_count;
-  for (int j0 = warp * 256; j0 < visited; j0 += 256 * W) {
-    unsigned slot[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int j = j0 + 32 * u + lane;
-      slot[u] = j < visited ? vlog[j] : 0xffffffffu;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (slot[u] != 0xffffffffu) vis[slot[u]] = 0u;
-  }
+  clear_visited(vis, vlog, ctl->vis_count, log_cap, a.vis_words, lane, warp, W);
   if (warp == 0 && lane == 0) {
     if (job.steps) *job.steps = steps;
     if (job.status) *job.status = status;
@@ -1375,7 +1291,7 @@ __global__ void __launch_bounds__(32 * W) search_kernel_wg(SearchArgs a, int sme
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WgCtl* ctl = reinterpret_cast<WgCtl*>(smem + smem_per_query);
   const WarpSmem lay = warp_smem_layout(kModePqU8, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
-  uint32_t* vis = a.vis + (static_cast<size_t>(blockIdx.x) << a.vis_log2);
+  uint32_t* vis = a.vis + static_cast<size_t>(blockIdx.x) * a.vis_words;
   uint32_t* vlog = a.vis_log + static_cast<size_t>(blockIdx.x) * a.vis_log_cap;
   for (;;) {
     if (threadIdx.x == 0) ctl->qi = atomicAdd(&a.counters[0], 1);
@@ -1428,7 +1344,7 @@ __global__ void serve_kernel(SearchArgs a, ServeArgs s, int smem_per_warp) {
   unsigned char* ws = smem + wib * smem_per_warp;
   const WarpSmem lay = warp_smem_layout(MODE, a.M, a.d, a.slot_bytes, a.depth, a.L, a.k, NB);
   const size_t gw = static_cast<size_t>(blockIdx.x) * warps + wib;
-  uint32_t* vis = a.vis + (gw << a.vis_log2);
+  uint32_t* vis = a.vis + gw * static_cast<size_t>(a.vis_words);
   uint32_t* vlog = a.vis_log + gw * static_cast<size_t>(a.vis_log_cap);
   constexpr int kPollEvery = 32;
   const bool poller = (gw % kPollEvery) == 0;
@@ -1627,28 +1543,11 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   p.warps_per_block = 1;
   // a warp group per query: PQ navigation only; W warps share one query
   p.wpq = (mode == kModePqU8 && (wpq == 2 || wpq == 4)) ? wpq : 1;
-  // Visited table: 2^15 slots (2^16 beyond L = 2048), doubled for R > 64.
-  // Measured on the 1M SIFT-like workload the largest visited set of 1,000
-  // queries is ~12k nodes up to L = 2048 and ~18.5k at L = 4096 (R = 64), so
-  // the 3/4-load overflow limit leaves a >= 2x margin, while 128 KB per warp
-  // keeps the tables of the resident warps in L2.  Smaller degrees keep the
-  // same size: at 10^7 nodes and R = 32 a query at L = 256 visited more than
-  // the 12,288 nodes a halved table would hold.
-  // Longer lists: 2^17 at L = 8192, 2^18 at L = 16384.  On indexes above
-  // 2^21 nodes a step finds more unseen neighbours (about 29 per step of
-  // R = 64 at 10^7 nodes, against about 9 at 10^6; a query takes about
-  // 1.6 L steps), so a query visits about 0.7 L R nodes there, twice that in
-  // the tail: the table holds 4 L R slots (3/4 of which may fill), up to 2^22.
-  int lg = L <= 2048 ? 15 : (L <= 4096 ? 16 : (L <= 8192 ? 17 : 18));
-  if (R > 64) ++lg;
-  if (n_index > (int64_t(1) << 21)) {
-    int want = 0;
-    while ((int64_t(1) << want) < 4ll * L * R) ++want;
-    if (want > 22) want = 22;
-    if (want > lg) lg = want;
-  }
-  p.vis_log2 = lg;
-  p.vis_log_cap = (3 << lg) / 4 + 32 * p.nb + 1;
+  // Visited set: one bit per node of the index, so it can neither overflow
+  // nor collide (one atomicOr per neighbour, no probing).  Words per query,
+  // rounded to 128 bytes; the clear log keeps up to kVisLog word indices.
+  p.vis_words = ((n_index > 0 ? n_index : 1) + 1023) / 1024 * 32;
+  p.vis_log_cap = kVisLog;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -83,15 +83,15 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   SearchPlan plan;
   cudaError_t e = plan_search(mode, a.R, a.M, a.d, slot_bytes, depth, L, k, nq, &plan, a.n);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
-  const size_t table_bytes = (size_t(1) << plan.vis_log2) * 4;
+  const size_t table_bytes = (size_t)plan.vis_words * 4;
   const size_t log_bytes = (size_t)plan.vis_log_cap * 4;
   const size_t per_warp = table_bytes + log_bytes;
   const size_t fit = (kScratchBytes - kHeader) / per_warp;
   if (fit < (size_t)kMinWarps)
     return set_error(ANN_EINVAL,
-                     "L=%d with R=%d needs %zu bytes of scratch per warp; the %zu MiB static "
+                     "an index of %d nodes needs %zu bytes of scratch per warp; the %zu MiB static "
                      "scratch must hold at least %d warps (use ann_search_dev)",
-                     L, a.R, per_warp, kScratchBytes >> 20, kMinWarps);
+                     a.n, per_warp, kScratchBytes >> 20, kMinWarps);
   const int64_t warps = (int64_t)plan.blocks * plan.warps_per_block;
   if (warps > (int64_t)fit) plan.blocks = (int)(fit / plan.warps_per_block);
   const size_t nwarps = (size_t)plan.blocks * plan.warps_per_block;
@@ -99,7 +99,7 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   a.counters = reinterpret_cast<int32_t*>(sb);
   a.expansions = reinterpret_cast<unsigned long long*>(sb + 64);
   a.vis = reinterpret_cast<uint32_t*>(sb + kHeader);
-  a.vis_log2 = plan.vis_log2;
+  a.vis_words = plan.vis_words;
   a.vis_log = reinterpret_cast<uint32_t*>(sb + kHeader + nwarps * table_bytes);
   a.vis_log_cap = plan.vis_log_cap;
   a.queries = queries;

@@ -226,8 +226,8 @@ int ann_serve_create(ann_index* ix, const ann_serve_cfg* cfg, ann_server** out) 
   const size_t nwarps = (size_t)s->plan.blocks * s->plan.warps_per_block;
   SV_TRY(cudaMalloc(&s->head_d, 3 * sizeof(unsigned long long)), "cudaMalloc serving head");
   SV_TRY(cudaMemset(s->head_d, 0, 3 * sizeof(unsigned long long)), "cudaMemset");
-  SV_TRY(cudaMalloc(&s->vis_d, (nwarps << s->plan.vis_log2) * 4), "cudaMalloc visited tables");
-  SV_TRY(cudaMemset(s->vis_d, 0, (nwarps << s->plan.vis_log2) * 4), "cudaMemset");
+  SV_TRY(cudaMalloc(&s->vis_d, nwarps * s->plan.vis_words * 4), "cudaMalloc visited sets");
+  SV_TRY(cudaMemset(s->vis_d, 0, nwarps * s->plan.vis_words * 4), "cudaMemset");
   SV_TRY(cudaMalloc(&s->vlog_d, nwarps * s->plan.vis_log_cap * 4), "cudaMalloc visited logs");
   SV_TRY(cudaMalloc(&s->counters_d, 4 * sizeof(int32_t)), "cudaMalloc counters");
   SV_TRY(cudaMemset(s->counters_d, 0, 4 * sizeof(int32_t)), "cudaMemset");
@@ -240,7 +240,7 @@ int ann_serve_create(ann_index* ix, const ann_serve_cfg* cfg, ann_server** out) 
   s->args.k = cfg->max_k;
   s->args.depth = cfg->depth;
   s->args.vis = s->vis_d;
-  s->args.vis_log2 = s->plan.vis_log2;
+  s->args.vis_words = s->plan.vis_words;
   s->args.vis_log = s->vlog_d;
   s->args.vis_log_cap = s->plan.vis_log_cap;
   s->args.counters = s->counters_d;
@@ -349,7 +349,7 @@ int ann_serve_poll(ann_server* s, uint64_t req_id, int32_t* ids, float* dists, i
     while (s->retired < s->published && s->consumed[s->retired % s->cfg.slots]) ++s->retired;
     s->reqs.erase(req_id);
   }
-  if (failed) return set_error(ANN_ENOMEM, "request %llu: %d queries overflowed their visited set",
+  if (failed) return set_error(ANN_ENOMEM, "request %llu: %d queries stopped early",
                                (unsigned long long)req_id, failed);
   return ANN_OK;
 }

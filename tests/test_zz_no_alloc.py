@@ -76,22 +76,33 @@ def test_noalloc_reports_status_and_rejects_oversized_scratch(small_index):
     ix.search_dev_noalloc(q, 10, 64, 2, ids, d, trace={"status": status})
     torch.cuda.synchronize()
     assert int(status.abs().sum()) == 0
-    # an index of degree 128 searched with L=4096 needs more than 16 MiB / 32
-    # of scratch per warp: rejected with a clear error
-    rng = np.random.default_rng(0)
-    n = 1000
-    base = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
-    adj = ((np.arange(n)[:, None] + 1 + rng.integers(0, n - 1, size=(n, 128))) % n).astype(np.int32)
-    wide = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
+    # an index of 4,000,000 nodes needs a 500,000-byte visited bitset per
+    # warp, plus its clear log: 32 warps do not fit in the 16 MiB static
+    # scratch, so the call is rejected with a clear error (exact navigation
+    # on a chain of 4-coordinate points keeps the index itself small)
+    n = 4_000_000
+    base = np.zeros((n, 4), np.uint8)
+    base[:, 0] = np.arange(n) % 256
+    adj = ((np.arange(n) + 1) % n).astype(np.int32)[:, None]
+    big = ann.Index(base, adj, 0, tier=ann.ANN_TIER_HBM)
     try:
         qw = torch.from_numpy(base[:4].copy()).cuda()
         with pytest.raises(ann.AnnError) as e:
-            wide.search_dev_noalloc(qw, 10, 4096, 1, ids[:4], d[:4])
+            big.search_dev_noalloc(qw, 2, 8, 1, ids[:4, :2].contiguous(), d[:4, :2].contiguous())
         assert e.value.status == ann._abi.ANN_EINVAL and "static" in str(e.value)
-        wide.search_dev_noalloc(qw, 10, 1024, 1, ids[:4], d[:4])   # within the limit
-        torch.cuda.synchronize()
     finally:
-        wide.close()
+        big.close()
+    small = ann.Index(base[:3_000_000], ((np.arange(3_000_000) + 1) % 3_000_000).astype(np.int32)[:, None],
+                      0, tier=ann.ANN_TIER_HBM)
+    try:   # 3,000,000 nodes fit (the limit is 3,931,136)
+        qw = torch.from_numpy(base[:4].copy()).cuda()
+        i2 = torch.empty((4, 2), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((4, 2), dtype=torch.float32, device="cuda")
+        small.search_dev_noalloc(qw, 2, 8, 1, i2, d2)
+        torch.cuda.synchronize()
+        assert i2.cpu().numpy()[:, 0].tolist() == [0, 1, 2, 3]
+    finally:
+        small.close()
 
 
 def test_noalloc_reports_mapped_ids(small_index):
