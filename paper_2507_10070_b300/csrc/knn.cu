@@ -447,21 +447,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // the 32 base norms of this chunk: one coalesced load, then shuffles
         const float xv = (j0 + lane < a.chunk_n) ? __ldg(a.xn + j0 + lane) : 0.f;
         const unsigned thr_d = static_cast<unsigned>(thr >> 32);
-        bool any = false;
+        // pass 1, converged: every distance, and the mask of the columns at
+        // or below this query's k-th best so far
+        unsigned cm = 0u;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float x = __shfl_sync(0xffffffffu, xv, j);
-          const float dist = fmaf(-2.f, __uint_as_float(r[j]), qn + x);
-          // columns past the chunk can never enter
-          r[j] = (j0 + j < a.chunk_n) ? static_cast<unsigned>(dist) : 0xffffffffu;
-          any |= r[j] <= thr_d;
+          r[j] = static_cast<unsigned>(fmaf(-2.f, __uint_as_float(r[j]), qn + x));
+          cm |= static_cast<unsigned>(r[j] <= thr_d && j0 + j < a.chunk_n) << j;
         }
-        if (!live || !any) continue;  // the common case: nothing below the k-th
+        if (!live || cm == 0u) continue;  // the common case: nothing below the k-th
+        // pass 2, this lane only: its few candidates, through a local copy
+        unsigned dl[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j0 + j >= a.chunk_n) break;
+        for (int j = 0; j < 32; ++j) dl[j] = r[j];
+        while (cm) {
+          const int j = __ffs(cm) - 1;
+          cm &= cm - 1u;
           const unsigned long long key =
-              (static_cast<unsigned long long>(r[j]) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
+              (static_cast<unsigned long long>(dl[j]) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
           if (key < thr) {
             int p = have < k ? have : k - 1;
             while (p > 0 && top[p - 1] > key) {
