@@ -100,6 +100,7 @@ struct SearchPlan {
   int smem_per_warp;   // bytes of one query's state
   int warps_per_block;
   int wpq;             // warps per query: 1, or 2 / 4 (one query per block, PQ mode)
+  bool pf;             // PQ mode, one warp, depth >= 2: the next-node prefetch instance
   int blocks;          // grid size (persistent)
   int tables;          // visited tables (and clear logs) the launch uses
   int64_t vis_words;   // words per visited bitset

@@ -467,7 +467,7 @@ __device__ __forceinline__ unsigned navigation_dist(const SearchArgs& a, const u
   return exact_dist_warp<MODE>(a, qs, w, lane);
 }
 
-template <int MODE, int NB>
+template <int MODE, int NB, bool PF = false>
 __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned char* ws,
                           const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int lane) {
   const long long t0 = global_timer_ns();
@@ -585,6 +585,54 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   int head = 0, inflight = 0, steps = 0, visited = 1, status = ANN_OK;
   int first_open = 0;  // every list entry before this position is selected
   const int max_steps = n + 1;  // each node is expanded at most once
+  // Next-node prefetch (PQ navigation, depth >= 2): once a step has the
+  // asymmetric distances of its node, the next node in the fetch FIFO --
+  // issued at least one step earlier, so its block has landed -- gets its
+  // code gathers and visited-bit atomics issued, and their round trip to
+  // L2/HBM overlaps this step's sort and merge.  The visited set sees the
+  // same inserts in the same order (the next node's atomics follow this
+  // node's, which have returned), and the list merge of its candidates still
+  // happens in its own step, so the search is unchanged.  A separate
+  // instance (PF), so that depths 0 and 1 keep the leaner kernel.
+  const bool prefetch = PF && MODE == kModePqU8 && D >= 2 && !a.grid_bar;
+  bool pre = false;  // the node at the FIFO head has its loads in flight
+  int pw[NB];
+  unsigned pword[NB], pold[NB];
+  uint4 pcode[NB][kMaxM / 16];
+  const int deg = a.R;
+  // read the ids of the block at `blk`, issue their code gathers and
+  // visited-bit atomics
+  auto issue_neighbours = [&](const unsigned char* blk, int (&w)[NB], unsigned (&word)[NB],
+                              uint4 (&code)[NB][kMaxM / 16], unsigned (&old)[NB]) {
+    // Neighbour ids are -1 padded, so the degree word need not be fetched.
+    const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + (MODE == kModePqU8 ? a.ids_off : 0));
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int j = t * 32 + lane;
+      int id = j < deg ? nbr[j] : -1;
+      if (id >= n) id = -1;  // validated at load; never trusted blindly
+      w[t] = id;
+      word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
+    }
+    // PQ codes of every listed neighbour, issued before the visited atomics
+    // so that both round trips overlap.
+    if (mode_pq(MODE)) {
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        if (w[t] >= 0) {
+          const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
+#pragma unroll
+          for (int c = 0; c < kMaxM / 16; ++c)
+            if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
+        }
+      }
+    }
+    // Visited set: one atomicOr per neighbour on its bit; the neighbour is
+    // new if its bit was clear (a repeated id in the row finds it set).
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
+  };
 
   for (;;) {
     // ---- a3: select the first candidate not chosen yet
@@ -651,42 +699,26 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
       }
       result_insert(res, s.nres, k, rkey, lane);
 
-      // ---- a7: neighbour ids and the visited set
-      // Neighbour ids are -1 padded, so the degree word need not be fetched.
-      const int deg = a.R;
-      const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + (MODE == kModePqU8 ? a.ids_off : 0));
+      // ---- a7: neighbour ids and the visited set (issued one step early
+      // when the node was prefetched)
       int w[NB];
       unsigned word[NB];
       bool fresh[NB];
-#pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        const int j = t * 32 + lane;
-        int id = j < deg ? nbr[j] : -1;
-        if (id >= n) id = -1;  // validated at load; never trusted blindly
-        w[t] = id;
-        word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
-      }
-      // PQ codes of every listed neighbour, issued before the visited probes
-      // so that both round trips overlap.
       uint4 code[NB][kMaxM / 16];
-      if (mode_pq(MODE)) {
+      unsigned old[NB];
+      if (pre) {
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
-          if (w[t] >= 0) {
-            const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
+          w[t] = pw[t];
+          word[t] = pword[t];
+          old[t] = pold[t];
 #pragma unroll
-            for (int c = 0; c < kMaxM / 16; ++c)
-              if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
-          }
+          for (int c = 0; c < kMaxM / 16; ++c) code[t][c] = pcode[t][c];
         }
+        pre = false;
+      } else {
+        issue_neighbours(blk, w, word, code, old);
       }
-      // Visited set: one atomicOr per neighbour on its bit, in flight
-      // together with the code loads above; the neighbour is new if its bit
-      // was clear (a repeated id in the row finds it set by the first).
-      unsigned old[NB];
-#pragma unroll
-      for (int t = 0; t < NB; ++t)
-        old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
 #pragma unroll
       for (int t = 0; t < NB; ++t) fresh[t] = w[t] >= 0 && ((old[t] >> (w[t] & 31)) & 1u) == 0u;
 
@@ -778,6 +810,14 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
         }
       }
 
+      // the next node's loads, overlapping the sort and merge below
+      if (prefetch && inflight >= 2) {
+        cp_async_wait_pending(inflight - 1);  // the next node's block (issued a step ago or more)
+        __syncwarp();
+        issue_neighbours(ring + head * slot_bytes, pw, pword, pcode, pold);
+        pre = true;
+      }
+
       // A key at or above the L-th entry of a full list cannot enter it.
       const unsigned long long thr = (s.len == L) ? s.keys[L - 1] : kNoKey;
 #pragma unroll
@@ -859,9 +899,10 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
                       : __int_as_float(0x7f800000);
   }
   // Clear the bits this query set, so the set is empty for the next query
-  // of this warp.
+  // of this warp.  (After an early stop a prefetched node's bits are not in
+  // the log: clear every word then.)
   __syncwarp();
-  clear_visited(vis, vlog, visited, log_cap, a.vis_words, lane, 0, 1);
+  clear_visited(vis, vlog, pre ? log_cap + 1 : visited, log_cap, a.vis_words, lane, 0, 1);
   if (lane == 0) {
     if (job.steps) *job.steps = steps;
     if (job.status) *job.status = status;
@@ -876,7 +917,7 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   __syncwarp();
 }
 
-template <int MODE, int NB>
+template <int MODE, int NB, bool PF = false>
 __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -905,7 +946,7 @@ __global__ void search_kernel(SearchArgs a, int smem_per_warp) {
     job.status = a.status ? a.status + qi : nullptr;
     job.t_begin = a.t_begin ? a.t_begin + qi : nullptr;
     job.t_end = a.t_end ? a.t_end + qi : nullptr;
-    run_query<MODE, NB>(a, job, ws, lay, vis, vlog, lane);
+    run_query<MODE, NB, PF>(a, job, ws, lay, vis, vlog, lane);
   }
   if (a.grid_bar) {
     // kernel-grained ablation: stop searching, but keep meeting the other
@@ -1437,13 +1478,13 @@ cudaError_t launch_serve_t(const SearchArgs& a, const ServeArgs& s, const Search
   return cudaGetLastError();
 }
 
-template <int MODE, int NB>
+template <int MODE, int NB, bool PF = false>
 cudaError_t launch_t(const SearchArgs& a, const SearchPlan& p, cudaStream_t st) {
   const int smem = p.smem_per_warp * p.warps_per_block;
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB, PF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  search_kernel<MODE, NB><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, p.smem_per_warp);
+  search_kernel<MODE, NB, PF><<<p.blocks, 32 * p.warps_per_block, smem, st>>>(a, p.smem_per_warp);
   return cudaGetLastError();
 }
 
@@ -1480,12 +1521,12 @@ cudaError_t occupancy_wg_t(int smem_block, int threads, int* blocks_per_sm) {
                                                        threads, smem_block);
 }
 
-template <int MODE, int NB>
+template <int MODE, int NB, bool PF = false>
 cudaError_t occupancy_t(int smem_block, int threads, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB>,
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<MODE, NB, PF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<MODE, NB>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<MODE, NB, PF>,
                                                        threads, smem_block);
 }
 
@@ -1493,6 +1534,19 @@ using LaunchFn = cudaError_t (*)(const SearchArgs&, const SearchPlan&, cudaStrea
 using OccFn = cudaError_t (*)(int, int, int*);
 
 int nb_index(int nb) { return nb == 1 ? 0 : (nb == 2 ? 1 : 2); }
+
+// PQ navigation with the next-node prefetch (depth >= 2, one warp per query)
+LaunchFn launch_pf_table(int nb) {
+  static const LaunchFn t[3] = {launch_t<kModePqU8, 1, true>, launch_t<kModePqU8, 2, true>,
+                                launch_t<kModePqU8, 4, true>};
+  return t[nb_index(nb)];
+}
+
+OccFn occ_pf_table(int nb) {
+  static const OccFn t[3] = {occupancy_t<kModePqU8, 1, true>, occupancy_t<kModePqU8, 2, true>,
+                             occupancy_t<kModePqU8, 4, true>};
+  return t[nb_index(nb)];
+}
 
 // Warp-group kernels: [nb][W == 4]
 LaunchFn launch_wg_table(int nb, int w) {
@@ -1553,8 +1607,11 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  p.pf = mode == kModePqU8 && p.wpq == 1 && depth >= 2;
   if (p.wpq > 1)
     e = occ_wg_table(p.nb, p.wpq)(p.smem_per_warp + kWgCtlBytes, 32 * p.wpq, &per_sm);
+  else if (p.pf)  // (never more blocks than the plain kernel: safe for the cooperative launch)
+    e = occ_pf_table(p.nb)(p.smem_per_warp * p.warps_per_block, 32 * p.warps_per_block, &per_sm);
   else
     e = occ_table(mode, p.nb)(p.smem_per_warp * p.warps_per_block, 32 * p.warps_per_block, &per_sm);
   if (e != cudaSuccess) return e;
@@ -1570,6 +1627,7 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
 
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
   if (plan.wpq > 1) return launch_wg_table(plan.nb, plan.wpq)(a, plan, stream);
+  if (plan.pf && !a.grid_bar) return launch_pf_table(plan.nb)(a, plan, stream);
   return launch_table(plan.mode, plan.nb)(a, plan, stream);
 }
 
