@@ -830,32 +830,37 @@ def run_large(args):
 def run_serving_workload(args):
     """Serving workload: 10^7 SIFT-like uint8 vectors (the 1M workload's
     generator: 256 centres, sigma 20), 10,000 queries.  The degree selector
-    picks R among {32, 48, 64, 96} (the GPU builder takes R <= 64), the
-    pipeline depth and the warps per query on random-link samples; Vamana at
-    that R is built on the GPU and stored breadth-first, with the node blocks
-    in host pinned memory and 32-byte PQ codes in HBM.  The operating point
-    is the smallest L of the sweep whose recall@10 reaches 0.95; there the
-    batched search is timed synchronously (depth 0) and relaxed, at 1, 2 and
-    4 warps per query.  The serving loop then takes a seeded Poisson stream
-    of request batches (size log-uniform in [1, 512], k in {10, 100}) at 70%
-    of its measured capacity, twice: with L in {L*, 1.25 L*, 1.5 L*} (the
-    operating point) and with the prescribed L in {64, 128, 256}."""
+    picks R among {32, 48, 64, 96}, the pipeline depth and the warps per
+    query on random-link samples; Vamana at that R is built on the GPU and
+    stored breadth-first, with the node blocks in host pinned memory and
+    32-byte PQ codes in HBM.  The operating point is the smallest L of the
+    sweep whose recall@10 reaches 0.95; there the batched search is timed
+    synchronously (depth 0) and relaxed, at 1, 2 and 4 warps per query.  The
+    serving loop then takes a seeded Poisson stream of request batches (size
+    log-uniform in [1, 512], k in {10, 100}) at 70% of its measured capacity,
+    twice: with L in {L*, 1.25 L*, 1.5 L*} (the operating point) and with the
+    prescribed L in {64, 128, 256}.  When the selector's R is not 64, the
+    operating point is also measured on an R = 64 graph, to check the choice
+    on the workload itself."""
     import torch
     import paper_2507_10070_b300 as ann
     torch.cuda.set_device(0)
     n, nq, M = args.serving_n, 10_000, 32
     t0 = time.time()
     at = ann.autotune_degree(degrees=(32, 48, 64, 96), n_sample=100_000, d=128, M=M, L=256, nq=2048, seed=1)
-    R = min(at["degree"], 64)
+    R = at["degree"]
     mx = datagen.sift_like()
     base, q = mx.base(n), mx.queries(nq)
     cb, codes = ann.build_pq(base, M, n_train=100_000, iters=25,
                              kpp_uniforms=datagen.kmeanspp_uniforms(mx.seed, M), encode_device="gpu")
-    adj, entry = ann.build_graph(base, R, 1.2, 128, seed=mx.seed, device="gpu")
     gt_ids, gt_d, gt_ms = ann.knn_exact(base, q, 100, return_ms=True)
-    b2, a2, e2, c2, old = ann.reorder_graph(base, adj, entry, codes)
-    del adj, codes
-    ix = ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
+
+    def build_index(degree):
+        adj, entry = ann.build_graph(base, degree, 1.2, 128, seed=mx.seed, device="gpu")
+        b2, a2, e2, c2, old = ann.reorder_graph(base, adj, entry, codes)
+        return ann.Index(b2, a2, e2, cb, c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
+
+    ix = build_index(R)
     ix_block_bytes = ix.block_bytes
     setup = time.time() - t0
     qd = torch.from_numpy(q).cuda()
@@ -865,38 +870,41 @@ def run_serving_workload(args):
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     depth_t = max(at["depth"], 1)   # the relaxed run; depth 0 is the synchronous baseline
 
-    def timed(L, depth, reps=2):
-        ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
-        ix.sync(st, check=False)
-        ms = []
-        for _ in range(reps):
-            with torch.cuda.stream(st):
-                flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
+    def operating_point(ix):
+        def timed(L, depth, reps=2):
             ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
-            e1.record(st)
-            s = ix.sync(st, check=False)
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        m = float(np.median(ms))
-        r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
-        return {"qps": round(nq / (m * 1e-3), 1), "recall_at_10": round(r, 4),
-                "visited_overflows": int(s.n_failed),
-                "mean_steps": round(s.expansions / max(s.queries, 1), 1),
-                "pcie_gbs": round(s.expansions * s.bytes_per_expansion / (m * 1e-3) / 1e9, 2)}
+            ix.sync(st, check=False)
+            ms = []
+            for _ in range(reps):
+                with torch.cuda.stream(st):
+                    flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ix.search_dev(qd, 10, L, depth, ids, dists, stream=st)
+                e1.record(st)
+                s = ix.sync(st, check=False)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            m = float(np.median(ms))
+            r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
+            return {"qps": round(nq / (m * 1e-3), 1), "recall_at_10": round(r, 4),
+                    "visited_overflows": int(s.n_failed),
+                    "mean_steps": round(s.expansions / max(s.queries, 1), 1),
+                    "pcie_gbs": round(s.expansions * s.bytes_per_expansion / (m * 1e-3) / 1e9, 2),
+                    "fetch_bytes_per_expansion": int(s.bytes_per_expansion)}
 
-    curve, L_star = [], None
-    for L in (128, 256, 512, 1024, 2048, 4096, 8192, 16384):
-        ix.search_dev(qd, 10, L, depth_t, ids, dists, stream=st)
-        s = ix.sync(st, check=False)
-        r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
-        curve.append({"L": L, "recall_at_10": round(r, 4), "visited_overflows": int(s.n_failed)})
-        if r >= 0.95:
-            L_star = L
-            break
-    op = {"L": L_star}
-    if L_star is not None:
+        curve, L_star = [], None
+        for L in (128, 256, 512, 1024, 2048, 4096, 8192, 16384):
+            ix.search_dev(qd, 10, L, depth_t, ids, dists, stream=st)
+            s = ix.sync(st, check=False)
+            r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
+            curve.append({"L": L, "recall_at_10": round(r, 4), "visited_overflows": int(s.n_failed)})
+            if r >= 0.95:
+                L_star = L
+                break
+        op = {"recall_curve": curve, "L": L_star}
+        if L_star is None:
+            return op
         by_w = {}
         for W in (1, 2, 4):
             ix.set_warps_per_query(W)
@@ -906,34 +914,47 @@ def run_serving_workload(args):
         op.update(depth=depth_t, warps_per_query=best_w, relaxed=by_w[str(best_w)],
                   sync=timed(L_star, 0), by_warps_per_query=by_w)
         op["relaxed_over_sync"] = round(op["relaxed"]["qps"] / op["sync"]["qps"], 4)
-        probe = ann.probe_read_bandwidth(1 << 30, 384, ann.ANN_TIER_HOST_PINNED, 64)
+        ix.set_warps_per_query(1)
+        return op
+
+    op = operating_point(ix)
+    L_star = op["L"]
+    fb = op["relaxed"]["fetch_bytes_per_expansion"] if L_star is not None else 384
+    if L_star is not None:
+        probe = ann.probe_read_bandwidth(1 << 30, fb, ann.ANN_TIER_HOST_PINNED, 64)
         # random reads over a region as large as this index's node blocks: the
         # host-memory translation caps them below the 1 GiB figure
         footprint = n * ix_block_bytes
-        probe_fp = ann.probe_read_bandwidth(footprint, 384, ann.ANN_TIER_HOST_PINNED, 16)
+        probe_fp = ann.probe_read_bandwidth(footprint, fb, ann.ANN_TIER_HOST_PINNED, 16)
         op["roofline"] = {"bound": "pcie", "achieved": op["relaxed"]["pcie_gbs"], "peak": round(probe, 2),
                           "unit": "GB/s", "frac": round(op["relaxed"]["pcie_gbs"] / probe, 4),
                           "peak_footprint": round(probe_fp, 2),
                           "frac_footprint": round(op["relaxed"]["pcie_gbs"] / probe_fp, 4),
-                          "what": ("relaxed search's storage-tier GB/s (expansions x 384 B) against random 384 B "
-                                   "reads of host pinned memory: over 1 GiB (peak) and over a region the size of "
-                                   "the index's node blocks (peak_footprint, %.1f GB)" % (footprint / 1e9))}
+                          "what": ("relaxed search's storage-tier GB/s (expansions x fetch bytes) against random "
+                                   "reads of the same size from host pinned memory: over 1 GiB (peak) and over a "
+                                   "region the size of the index's node blocks (peak_footprint, %.1f GB)"
+                                   % (footprint / 1e9))}
     with ClockSampler(0) as clk:
-        Ls_op = None if L_star is None else sorted({min(x, 16384) for x in (
-            L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32)})
         serving_op = None
-        if Ls_op is not None:
+        if L_star is not None:
+            Ls_op = sorted({min(x, 16384) for x in (L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32)})
             serving_op = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], L_star, depth_t,
                                      args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=Ls_op,
-                                     probe_gbps=op["roofline"]["peak"])
+                                     probe_gbps=op["roofline"]["peak"], fetch_bytes=fb)
         serving_spec = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], 128, depth_t,
-                                   args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=(64, 128, 256))
+                                   args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=(64, 128, 256),
+                                   probe_gbps=op.get("roofline", {}).get("peak"), fetch_bytes=fb)
     ix.close()
-    return {"what": run_serving_workload.__doc__.split("\n\n")[0].replace("\n", " "),
-            "n": n, "nq": nq, "M": M, "R": R, "autotune": at, "recall_curve": curve,
-            "operating_point": op, "serving_at_operating_point": serving_op,
-            "serving_prescribed_L": serving_spec, "clocks": clk.summary(),
-            "ground_truth_ms": round(gt_ms, 1), "setup_s": round(setup, 1)}
+    out = {"what": run_serving_workload.__doc__.split("\n\n")[0].replace("\n", " "),
+           "n": n, "nq": nq, "M": M, "R": R, "autotune": at, "recall_curve": op["recall_curve"],
+           "operating_point": op, "serving_at_operating_point": serving_op,
+           "serving_prescribed_L": serving_spec, "clocks": clk.summary(),
+           "ground_truth_ms": round(gt_ms, 1), "setup_s": round(setup, 1)}
+    if R != 64:
+        ix64 = build_index(64)
+        out["operating_point_R64"] = operating_point(ix64)
+        ix64.close()
+    return out
 
 
 def cpu_baseline(w, L: int, sample: int, depth: int = 0):

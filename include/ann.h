@@ -433,7 +433,7 @@ int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
  * vectors in HBM), RobustPrune runs one warp per node, and back edges are
  * grouped by a device sort.  The candidate pool of a node is the L_build
  * expanded nodes nearest to it.  Deterministic.  Needs d % 16 == 0,
- * 1 <= R <= 64, R <= L_build <= 256 - R.  Uses the current device; host
+ * 1 <= R <= 128, R <= L_build <= 256 - R.  Uses the current device; host
  * buffers in and out, as ann_build_graph.
  */
 int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,

@@ -109,8 +109,13 @@ struct SearchPlan {
 
 // Per-warp shared-memory layout (byte offsets), identical on host and device.
 struct WarpSmem {
-  int lut, ring, q, keys, flags, res, cand, rank, ring_key, total;
+  int lut, ring, q, keys, flags, res, cand, rank, ring_key, pkeys, pflags, total;
 };
+
+// Entries of a query's pending buffer: the sorted candidates of the latest
+// steps, merged into the list only when it fills (see run_query).
+constexpr int kPend = 128;
+constexpr int kLazyL = 2048;  // lists at least this long use the pending buffer
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -136,9 +141,13 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int mode, int M, int d, int
   s.ring_key = off;
   off += (depth + 1) * 8;
   s.rank = off;
-  off += 32 * nb * 4;
+  off += (32 * nb > kPend ? 32 * nb : kPend) * 4;
+  s.pkeys = off;
+  off += kPend * 8;
   s.flags = off;
   off += align_up(L, 16);
+  s.pflags = off;
+  off += kPend;
   s.total = align_up(off, 128);
   return s;
 }

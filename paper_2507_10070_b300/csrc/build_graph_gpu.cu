@@ -282,11 +282,11 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
                                    int32_t* entry_out) {
   if (!base || !adj_out) return set_error(ANN_EINVAL, "ann_build_graph_gpu: NULL buffer");
   if (dtype != ANN_U8 && dtype != ANN_F32) return set_error(ANN_EINVAL, "ann_build_graph_gpu: unknown dtype");
-  if (n < 2 || n >= INT32_MAX || R < 1 || R > 64 || L_build < R || L_build > kCandMax - R ||
+  if (n < 2 || n >= INT32_MAX || R < 1 || R > kMaxR || L_build < R || L_build > kCandMax - R ||
       d < 16 || d % 16 || d > kMaxD || !(alpha >= 1.0f))
     return set_error(ANN_EINVAL,
-                     "ann_build_graph_gpu: need 2 <= n, 1 <= R <= 64, R <= L_build <= %d - R, d %% 16 == 0 "
-                     "(n=%lld d=%d R=%d L=%d)", kCandMax, (long long)n, d, R, L_build);
+                     "ann_build_graph_gpu: need 2 <= n, 1 <= R <= %d, R <= L_build <= %d - R, d %% 16 == 0 "
+                     "(n=%lld d=%d R=%d L=%d)", kMaxR, kCandMax, (long long)n, d, R, L_build);
   const int elt = dtype == ANN_U8 ? 1 : 4;
   const int row_bytes = d * elt;
   const int stride = align_up(R, 4);

@@ -146,6 +146,23 @@ __device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int 
   return lo;
 }
 
+// The r-th smallest (0-based) of the union of sorted, distinct a[0..na) and
+// b[0..nb), r < na + nb: take i from a and r+1-i from b, the smallest i for
+// which a[i] follows b[r-i].
+__device__ __forceinline__ unsigned long long kth_of_two(const unsigned long long* a, int na,
+                                                         const unsigned long long* b, int nb, int r) {
+  int lo = r + 1 - nb > 0 ? r + 1 - nb : 0;
+  int hi = r + 1 < na ? r + 1 : na;
+  while (lo < hi) {
+    const int i = (lo + hi) >> 1;
+    if (a[i] < b[r - i]) lo = i + 1; else hi = i;
+  }
+  const int j = r + 1 - lo;
+  const unsigned long long x = lo > 0 ? a[lo - 1] : 0ull;
+  const unsigned long long y = j > 0 ? b[j - 1] : 0ull;
+  return x > y ? x : y;
+}
+
 // ---- Kernel-grained I/O, the ablation of the query-grained I/O stack
 // (Section "Resource-Efficient Query-Grained Concurrent I/O Stack" compares
 // against CAM, where the kernel waits for every request of the batch): with
@@ -261,7 +278,8 @@ __device__ __forceinline__ void result_insert(unsigned long long* res, int& nres
 // Entries before rank_0 keep their place.  Returns rank_0 (the first position
 // whose entry changed), or L if nothing entered.
 __device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned long long* cand,
-                                                int c, int L, int lane) {
+                                                int c, int L, int lane,
+                                                const unsigned char* cflags = nullptr) {
   if (c == 0) return L;
   if (s.len == L && cand[0] > s.keys[L - 1]) return L;  // nothing would enter
   for (int j = lane; j < c; j += 32) s.rank[j] = lower_bound_u64(s.keys, s.len, cand[j]);
@@ -309,7 +327,7 @@ __device__ __forceinline__ int merge_candidates(QueryState& s, const unsigned lo
     const int np = j + s.rank[j];
     if (np < L) {
       s.keys[np] = cand[j];
-      s.flags[np] = 0;
+      s.flags[np] = cflags ? cflags[j] : 0;
     }
   }
   __syncwarp();
@@ -486,6 +504,23 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   s.keys = reinterpret_cast<unsigned long long*>(ws + lay.keys);
   s.flags = ws + lay.flags;
   s.rank = reinterpret_cast<int*>(ws + lay.rank);
+  // Pending buffer: each step's entering candidates are merged into this
+  // short sorted buffer, and the buffer into the list only when it is full,
+  // so the list's tail moves once per many steps instead of every step.  The
+  // candidate list of the search is the first L entries of the union of the
+  // two: selection takes the first unselected entry of the union if its rank
+  // in the union is below L, and the bound for entering is the union's L-th
+  // key.  An entry pushed past rank L never returns (the union only grows
+  // until a merge drops such entries), so this is the same list.  Used from
+  // L = kLazyL on: below it the tail is short, and merging straight into the
+  // list costs less than the union's bookkeeping.
+  const bool lazy = L >= kLazyL;
+  QueryState pend;
+  pend.keys = reinterpret_cast<unsigned long long*>(ws + lay.pkeys);
+  pend.flags = ws + lay.pflags;
+  pend.rank = s.rank;
+  pend.len = 0;
+  int pfirst_open = 0;  // every pending entry before this position is selected
 
   // ---- query vector into shared memory
   if (job.query) {
@@ -635,26 +670,47 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   };
 
   for (;;) {
-    // ---- a3: select the first candidate not chosen yet
-    int sel = -1;
+    // ---- a3: select the first candidate not chosen yet: the first
+    // unselected entry of the list or of the pending buffer, whichever is
+    // smaller, if its rank in their union is below L
+    int ia = -1, ib = -1;
     for (int b = first_open; b < s.len; b += 32) {
       const int i = b + lane;
       const unsigned m = __ballot_sync(kFull, i < s.len && s.flags[i] == 0);
       if (m) {
-        sel = b + __ffs(m) - 1;
+        ia = b + __ffs(m) - 1;
         break;
       }
     }
-    first_open = sel >= 0 ? sel + 1 : s.len;
+    for (int b = pfirst_open; b < pend.len; b += 32) {
+      const int i = b + lane;
+      const unsigned m = __ballot_sync(kFull, i < pend.len && pend.flags[i] == 0);
+      if (m) {
+        ib = b + __ffs(m) - 1;
+        break;
+      }
+    }
+    first_open = ia >= 0 ? ia : s.len;
+    pfirst_open = ib >= 0 ? ib : pend.len;
+    int sel = -1;  // 0: list entry ia, 1: pending entry ib
+    unsigned long long key = 0;
+    if (ia >= 0 && (ib < 0 || s.keys[ia] < pend.keys[ib])) {
+      key = s.keys[ia];
+      if (pend.len == 0 || ia + lower_bound_u64(pend.keys, pend.len, key) < L) sel = 0;
+    } else if (ib >= 0) {
+      key = pend.keys[ib];
+      if (ib + lower_bound_u64(s.keys, s.len, key) < L) sel = 1;
+    }
+    if (sel == 0) first_open = ia + 1;
+    if (sel == 1) pfirst_open = ib + 1;
     if (sel >= 0) {
       // ---- a4: issue the fetch of its block into the next ring slot
-      const unsigned long long key = s.keys[sel];
       const unsigned v = static_cast<unsigned>(key);
       int slot = head + inflight;
       if (slot > D) slot -= D + 1;
       __syncwarp();
       if (lane == 0) {
-        s.flags[sel] = 1;
+        if (sel == 0) s.flags[ia] = 1; else pend.flags[ib] = 1;
         ring_key[slot] = key;
       }
       const uint8_t* src = (MODE == kModePqU8)
@@ -818,8 +874,11 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
         pre = true;
       }
 
-      // A key at or above the L-th entry of a full list cannot enter it.
-      const unsigned long long thr = (s.len == L) ? s.keys[L - 1] : kNoKey;
+      // A key at or above the L-th entry of a full list cannot enter it (the
+      // list is the first L entries of list and pending buffer together).
+      const unsigned long long thr =
+          pend.len == 0 ? (s.len == L ? s.keys[L - 1] : kNoKey)
+                        : (s.len + pend.len >= L ? kth_of_two(s.keys, s.len, pend.keys, pend.len, L - 1) : kNoKey);
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (!fresh[t]) key[t] = kNoKey;
@@ -869,9 +928,21 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
           for (int t = 0; t < NB; ++t) cand[t * 32 + lane] = key[t];
           __syncwarp();
         }
-        if (c > 0) {
+        if (c > 0 && !lazy) {
           const int changed = merge_candidates(s, cand, c, L, lane);
           if (changed < first_open) first_open = changed;
+        } else if (c > 0) {
+          if (pend.len + c > kPend) {
+            // the pending buffer is full: merge it, selected flags and all,
+            // into the list (entries past rank L fall off), then empty it
+            const int changed = merge_candidates(s, pend.keys, pend.len, L, lane, pend.flags);
+            if (changed < first_open) first_open = changed;
+            pend.len = 0;
+            pfirst_open = 0;
+            __syncwarp();
+          }
+          const int pchanged = merge_candidates(pend, cand, c, kPend, lane);
+          if (pchanged < pfirst_open) pfirst_open = pchanged;
         }
       }
       __syncwarp();

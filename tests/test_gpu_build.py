@@ -62,12 +62,30 @@ def test_gpu_build_f32_inmemory_workload():
     assert oracle.recall_at_k(ids, gi, gd, d) >= 0.95
 
 
+def test_gpu_build_degree_96_matches_host_quality():
+    """R = 96 (the degree selector's pick on some samples): rows of up to 96
+    ids, reachability, and search quality within 0.01 of the host builder."""
+    mx = datagen.sift_like()
+    base, q = mx.base(20_000), mx.queries(200)
+    g_adj, g_entry = ann.build_graph(base, 96, 1.2, 128, seed=7, device="gpu")
+    h_adj, h_entry = ann.build_graph(base, 96, 1.2, 128, seed=7, device="cpu")
+    _check_rows(g_adj, 96)
+    assert (g_adj >= 0).sum(1).max() > 64                   # rows use the larger degree
+    assert _reach(g_adj, g_entry) >= 0.999 * base.shape[0]
+    gi, gd = oracle.knn(base, q, 10)
+    ig, dg, _ = oracle.search(base, g_adj, g_entry, q, 10, 48, 0)
+    ih, dh, _ = oracle.search(base, h_adj, h_entry, q, 10, 48, 0)
+    assert oracle.recall_at_k(ig, gi, gd, dg) >= oracle.recall_at_k(ih, gi, gd, dh) - 0.01
+
+
 def test_gpu_build_rejects_bad_sizes():
     x = np.zeros((100, 8), np.uint8)
     with pytest.raises(ann.AnnError):
         ann.build_graph(x, 16, device="gpu")                 # d % 16 != 0
     with pytest.raises(ann.AnnError):
-        ann.build_graph(np.zeros((100, 16), np.uint8), 96, L_build=128, device="gpu")   # R > 64
+        ann.build_graph(np.zeros((100, 16), np.uint8), 130, L_build=126, device="gpu")   # R > 128
+    with pytest.raises(ann.AnnError):
+        ann.build_graph(np.zeros((100, 16), np.uint8), 96, L_build=192, device="gpu")    # L_build > 256 - R
 
 
 def test_gpu_pq_encoder_equals_host_encoder():

@@ -44,6 +44,20 @@ def test_pq_search_bit_exact(u8_pq, pq_index, L, depth):
     assert stats.expansions == int(osteps.sum())
 
 
+@pytest.mark.parametrize("L", [2048, 4096])
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_pq_search_long_lists_bit_exact(u8_pq, pq_index, L, depth):
+    """From L = 2048 on, each step's candidates go to a short sorted pending
+    buffer merged into the list only when full; selection and the entry bound
+    work on the union.  The list, and so every step, must stay the oracle's."""
+    q = u8_pq["q"][:48]
+    ids, dists, stats, tr = pq_index.search(q, 10, L, depth, trace=True)
+    oi, od, osteps = _oracle_pq(u8_pq, 10, L, depth, q=q)
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], osteps)
+
+
 @pytest.mark.parametrize("k,L", [(1, 1), (1, 8), (33, 40), (100, 128), (256, 512), (10, 1536)])
 def test_pq_search_k_and_L_extremes(u8_pq, pq_index, k, L):
     ids, dists, _ = pq_index.search(u8_pq["q"][:97], k, L, 1)
