@@ -760,7 +760,8 @@ def run_large(args):
     if args.serve_seconds > 0:
         out["serving"] = run_serving(ix, {"q": q}, gt_ids, gt_d, L, best, args.serve_seconds)
     # ---- the operating point: the smallest L of the sweep with recall@10 >=
-    # 0.95, timed synchronously and relaxed at 1, 2 and 4 warps per query
+    # 0.95, timed synchronously, relaxed at depths 1, 2 and 4, and at 2 and
+    # 4 warps per query at the best of those depths
     curve, L_star = [], None
     for Lc in args.large_sweep_Ls:
         ix.search_dev(qd, k, Lc, best, ids, dists, stream=stream)
@@ -788,18 +789,21 @@ def run_large(args):
             return {"qps": round(nq / (ms * 1e-3), 1), "mean_steps": round(s_.expansions / max(s_.queries, 1), 1),
                     "pcie_gbs": round(s_.expansions * s_.bytes_per_expansion / (ms * 1e-3) / 1e9, 2),
                     "recall_at_10": round(ann.recall_at_k(ids.cpu().numpy(), gt_ids, gt_d, dists.cpu().numpy()), 4)}
-        by_w = {}
-        for W in (1, 2, 4):
+        # the pipeline depth is chosen again at this L (a longer search
+        # leaves more to overlap), then warps per query at that depth
+        by_d = {str(dd): timed_at(dd) for dd in (0, 1, 2, 4)}
+        d_star = max((1, 2, 4), key=lambda dd: by_d[str(dd)]["qps"])
+        by_w = {"1": by_d[str(d_star)]}
+        for W in (2, 4):
             ix.set_warps_per_query(W)
-            by_w[str(W)] = timed_at(best)
+            by_w[str(W)] = timed_at(d_star)
         best_w = int(max(by_w, key=lambda x: by_w[x]["qps"]))
-        ix.set_warps_per_query(best_w)
-        op.update(depth=best, warps_per_query=best_w, relaxed=by_w[str(best_w)], by_warps_per_query=by_w,
-                  sync=timed_at(0))
+        op.update(depth=d_star, warps_per_query=best_w, relaxed=by_w[str(best_w)], by_depth=by_d,
+                  by_warps_per_query=by_w, sync=by_d["0"])
         op["relaxed_over_sync"] = round(op["relaxed"]["qps"] / op["sync"]["qps"], 4)
         ix.set_warps_per_query(1)
         if args.serve_seconds > 0:
-            op["serving"] = run_serving(ix, {"q": q}, gt_ids, gt_d, L_star, best, args.serve_seconds,
+            op["serving"] = run_serving(ix, {"q": q}, gt_ids, gt_d, L_star, d_star, args.serve_seconds,
                                         Ls=sorted({min(x, 16384) for x in (L_star, int(L_star * 1.25) // 32 * 32,
                                                                            int(L_star * 1.5) // 32 * 32)}))
     out["operating_point"] = op
@@ -835,7 +839,8 @@ def run_serving_workload(args):
     stored breadth-first, with the node blocks in host pinned memory and
     32-byte PQ codes in HBM.  The operating point is the smallest L of the
     sweep whose recall@10 reaches 0.95; there the batched search is timed
-    synchronously (depth 0) and relaxed, at 1, 2 and 4 warps per query.  The
+    synchronously (depth 0) and relaxed at depths 1, 2 and 4, and at 2 and 4
+    warps per query at the best of those depths.  The
     serving loop then takes a seeded Poisson stream of request batches (size
     log-uniform in [1, 512], k in {10, 100}) at 70% of its measured capacity,
     twice: with L in {L*, 1.25 L*, 1.5 L*} (the operating point) and with the
@@ -894,7 +899,7 @@ def run_serving_workload(args):
                     "fetch_bytes_per_expansion": int(s.bytes_per_expansion)}
 
         curve, L_star = [], None
-        for L in (128, 256, 512, 1024, 2048, 4096, 8192, 16384):
+        for L in (128, 256, 512, 1024, 2048, 4096, 6144, 8192, 12288, 16384):
             ix.search_dev(qd, 10, L, depth_t, ids, dists, stream=st)
             s = ix.sync(st, check=False)
             r = ann.recall_at_k(ids.cpu().numpy(), gt_ids[:, :10], gt_d[:, :10], dists.cpu().numpy())
@@ -905,20 +910,24 @@ def run_serving_workload(args):
         op = {"recall_curve": curve, "L": L_star}
         if L_star is None:
             return op
-        by_w = {}
-        for W in (1, 2, 4):
+        # the depth is chosen again at this L (the selector's came from short
+        # searches on samples), then warps per query at that depth
+        by_d = {str(dd): timed(L_star, dd) for dd in (0, 1, 2, 4)}
+        d_star = max((1, 2, 4), key=lambda dd: by_d[str(dd)]["qps"])
+        by_w = {"1": by_d[str(d_star)]}
+        for W in (2, 4):
             ix.set_warps_per_query(W)
-            by_w[str(W)] = timed(L_star, depth_t)
+            by_w[str(W)] = timed(L_star, d_star)
         best_w = int(max(by_w, key=lambda x: by_w[x]["qps"]))
-        ix.set_warps_per_query(best_w)
-        op.update(depth=depth_t, warps_per_query=best_w, relaxed=by_w[str(best_w)],
-                  sync=timed(L_star, 0), by_warps_per_query=by_w)
+        op.update(depth=d_star, warps_per_query=best_w, relaxed=by_w[str(best_w)],
+                  sync=by_d["0"], by_depth=by_d, by_warps_per_query=by_w)
         op["relaxed_over_sync"] = round(op["relaxed"]["qps"] / op["sync"]["qps"], 4)
         ix.set_warps_per_query(1)
         return op
 
     op = operating_point(ix)
     L_star = op["L"]
+
     fb = op["relaxed"]["fetch_bytes_per_expansion"] if L_star is not None else 384
     if L_star is not None:
         probe = ann.probe_read_bandwidth(1 << 30, fb, ann.ANN_TIER_HOST_PINNED, 64)
@@ -938,7 +947,7 @@ def run_serving_workload(args):
         serving_op = None
         if L_star is not None:
             Ls_op = sorted({min(x, 16384) for x in (L_star, int(L_star * 1.25) // 32 * 32, int(L_star * 1.5) // 32 * 32)})
-            serving_op = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], L_star, depth_t,
+            serving_op = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], L_star, op["depth"],
                                      args.serve_seconds if args.serve_seconds > 0 else 8.0, Ls=Ls_op,
                                      probe_gbps=op["roofline"]["peak"], fetch_bytes=fb)
         serving_spec = run_serving(ix, {"q": q}, gt_ids[:, :10], gt_d[:, :10], 128, depth_t,
@@ -1034,8 +1043,9 @@ def run_kernel_case(args):
     nav     FP32 / BF16 / FP8-E4M3 navigation and the FP32 rerank on 10^6
             DEEP-like float32 vectors (graph R=48 built on the GPU), vectors
             in HBM, --case-nq queries at --case-L, 2 launches each
-    knn     brute-force ground truth: 10^6 SIFT-like vectors x --case-nq
-            queries, tensor-core engine then CUDA-core engine, k=10
+    knn     brute-force ground truth: --case-knn-n SIFT-like vectors (10^6
+            by default) x --case-nq queries, tensor-core engine then
+            CUDA-core engine, k=10
     build   index tooling: GPU PQ encoding and Vamana on the GPU (R=64,
             L_build=128) over 200,000 SIFT-like vectors"""
     import torch
@@ -1110,10 +1120,12 @@ def run_kernel_case(args):
             ix.close()
     elif case == "knn":
         mx = datagen.sift_like()
-        base, q = mx.base(1_000_000), mx.queries(nq)
+        nb = args.case_knn_n
+        base, q = mx.base(nb), mx.queries(nq)
         for eng in ("tensor", "cuda"):
             _, _, ms = ann.knn_exact(base, q, 10, engine=eng, return_ms=True)
-            out[eng] = {"ms": round(ms, 3), "tflops": round(2e6 * nq * 128 / (ms * 1e-3) / 1e12, 2)}
+            out[eng] = {"ms": round(ms, 3), "tflops": round(2 * nb * nq * 128 / (ms * 1e-3) / 1e12, 2)}
+        out["n"] = nb
     elif case == "build":
         mx = datagen.sift_like()
         base = mx.base(200_000)
@@ -1165,12 +1177,13 @@ def main():
     ap.add_argument("--large-n", type=int, default=100_000_000)
     ap.add_argument("--large-L", type=int, default=128)
     ap.add_argument("--large-Lb", type=int, default=128, help="L_build of the large index")
-    ap.add_argument("--large-sweep-Ls", type=int, nargs="+", default=[512, 2048, 4096, 8192, 12288, 16384],
+    ap.add_argument("--large-sweep-Ls", type=int, nargs="+", default=[512, 2048, 4096, 5120, 6144, 8192, 12288, 16384],
                     help="list sizes tried for the large workload's recall@10 >= 0.95 operating point")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only print the storage-tier probe's GB/s for several read sizes")
     ap.add_argument("--kernel-case", choices=["search", "serve", "nav", "knn", "build"],
                     help="only run one small, fixed invocation of a kernel family (for ncu captures)")
+    ap.add_argument("--case-knn-n", type=int, default=1_000_000, help="base rows of the knn kernel case")
     ap.add_argument("--case-nq", type=int, default=1000)
     ap.add_argument("--case-L", type=int, default=1280)
     ap.add_argument("--case-depth", type=int, default=1)

@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cfloat>
 #include <cstdint>
 #include <mutex>
 
@@ -160,19 +161,34 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 // top-k selection runs in the same kernel on the accumulator, so the
 // distance matrix never goes to HBM.
 //
-// Per CTA (one query tile x a contiguous range of base tiles), 12 warps:
-//   warp 0 (one lane)  TMA producer: the query tile once, then base tiles into
-//                      a ring of kStages shared-memory stages (128-byte
-//                      swizzled, one 64-coordinate "atom" = 128 B per row);
-//   warp 1 (one lane)  MMA issuer: d/16 MMAs per base tile into one of two
-//                      tensor-memory accumulators (128 lanes x 128 columns);
-//                      tcgen05.commit frees the stage and publishes the
-//                      accumulator;
-//   warps 4-7, 8-11    two epilogue warpgroups, one per accumulator: thread t
-//                      of warp w reads row 32*(w%4)+t (one query) with
-//                      tcgen05.ld and keeps that query's ascending top-k of
-//                      (distance, id) keys; a key enters only if it is below
-//                      the k-th (one compare per distance).
+// Per CTA (two query tiles x a contiguous range of base tiles), 20 warps:
+//   warp 0 (one lane)  TMA producer: the two query tiles once, then base
+//                      tiles into a ring of kTcStages shared-memory stages
+//                      (128-byte swizzled, one 64-coordinate "atom" = 128 B
+//                      per row), and each tile's 128 base norms (a bulk copy)
+//                      into a ring of kNormRing slots;
+//   warp 1 (one lane)  MMA issuer: for each base tile, d/16 MMAs per query
+//                      tile into one of two accumulator pairs (4 x 128
+//                      tensor-memory columns, all 512); tcgen05.commit frees
+//                      the stage and publishes the pair;
+//   warps 4-19         four epilogue warpgroups, one per accumulator (query
+//                      tile qt, buffer b): thread t of warp w reads row
+//                      32*(w%4)+t of its query tile with tcgen05.ld and keeps
+//                      that query's ascending top-k of (distance, id) keys.
+// Two query tiles share each base tile, which halves the base's L2 traffic.
+// The epilogue works on v = |x|^2 - 2 q.x (the query's own |q|^2 is a
+// constant of its ranking) against the bound k-th distance - |q|^2: one FMA
+// per distance and a tree of 3-input mins, then one compare per 32 columns;
+// only a lane whose minimum is within the bound looks at its candidates one
+// by one (after the first tiles, the common case is that none is).  The next
+// 32 columns load from tensor memory while the current ones are scanned, and
+// the accumulator goes back to the MMA as soon as its last columns are in
+// registers.  Base norms are padded to whole tiles with +inf, so rows past
+// the end never qualify.  The bound starts at the running k-th best of the
+// chunks already folded, and the CTAs of a query share a distance bound in
+// global memory: each lowers it (atomicMin) to its own k-th distance and
+// reads it once per tile, so a CTA's first tiles no longer admit a stream of
+// candidates that another CTA has already ruled out.
 // Each warpgroup writes its lists as one part; a fold kernel merges the parts
 // with the running top-k after each chunk of the base.
 // Every wait on an mbarrier is bounded: past ~2 s the CTA sets an abort flag,
@@ -181,16 +197,17 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 
 constexpr int kTcM = 128;            // queries per CTA (MMA M)
 constexpr int kTcN = 128;            // base rows per tile (MMA N)
+constexpr int kTcQT = 2;             // query tiles per CTA
 constexpr int kTcStages = 4;         // base-tile ring
+constexpr int kNormRing = 8;         // base-norm slots (one tile each)
 constexpr int kAtomBytes = 128 * 128;  // one 64-coordinate BF16 atom of a 128-row tile
-constexpr int kTcThreads = 384;
+constexpr int kTcThreads = 128 + 4 * 128;
 constexpr long long kTcWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 struct TcArgs {
   const float* qn;          // [nq] query norms
-  const float* xn;          // [chunk_n] base-row norms of this chunk
+  const float* xn;          // [tiles * 128] base-row norms of this chunk, +inf past its rows
   int64_t nq;
-  int32_t chunk_n;          // rows of this chunk
   int64_t id0;              // id of the chunk's first row
   int32_t tiles;            // base tiles in the chunk
   int32_t splits;           // CTAs per query tile
@@ -198,6 +215,7 @@ struct TcArgs {
   int32_t k;
   int32_t nslots;           // parts per query: 1 (running) + 2 * splits
   unsigned long long* keys; // [nq][nslots][k]
+  unsigned* bound;          // [nq] a distance no query's k-th best exceeds, shared by all CTAs
   int* error;               // set to 1 if a wait ran out
 };
 
@@ -300,19 +318,46 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+#define ANN_R32_OUT(r)                                                                                  \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),            \
+      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),   \
+      "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), \
+      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define ANN_R32_INOUT(r)                                                                                \
+  "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),            \
+      "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),   \
+      "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), \
+      "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+
+// Start loading 32 consecutive accumulator columns of this thread's lane;
+// the registers are valid only after tmem_wait(r).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : ANN_R32_OUT(r)
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Wait for this thread's tensor-memory loads; naming the registers as
+// operands keeps every use of them after the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : ANN_R32_INOUT(r) : : "memory");
+}
+
+// Plain (untiled) bulk copy global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(sh_u32(dst)), "l"(src), "r"(bytes), "r"(sh_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -322,20 +367,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // 1024-byte alignment for the swizzled operand tiles
   const uint32_t raw = sh_u32(tc_smem_raw);
   unsigned char* smem = tc_smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  unsigned char* sA = smem;                                   // natoms x 16 KB
-  unsigned char* sB = smem + 2 * kAtomBytes;                  // kTcStages x natoms x 16 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * 2 * kAtomBytes);
+  unsigned char* sA = smem;                                   // kTcQT x 2 atoms x 16 KB
+  unsigned char* sB = smem + kTcQT * 2 * kAtomBytes;          // kTcStages x 2 atoms x 16 KB
+  float* sN = reinterpret_cast<float*>(sB + kTcStages * 2 * kAtomBytes);  // kNormRing x 128 base norms
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sN + kNormRing * kTcN);
   uint64_t* full = bars;                    // [kTcStages]
   uint64_t* empty = bars + kTcStages;       // [kTcStages]
   uint64_t* a_full = bars + 2 * kTcStages;  // [1]
   uint64_t* acc_full = a_full + 1;          // [2]
   uint64_t* acc_empty = a_full + 3;         // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 5);
+  uint64_t* n_full = a_full + 5;            // [kNormRing]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(n_full + kNormRing);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int natoms = a.natoms;
-  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kTcM;
+  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * (kTcQT * kTcM);
   const int s = blockIdx.y;
   const int t_lo = static_cast<int>((static_cast<int64_t>(a.tiles) * s) / a.splits);
   const int t_hi = static_cast<int>((static_cast<int64_t>(a.tiles) * (s + 1)) / a.splits);
@@ -349,15 +396,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(a_full, 1);
     mbar_init(acc_full + 0, 1);
     mbar_init(acc_full + 1, 1);
-    mbar_init(acc_empty + 0, 4);
-    mbar_init(acc_empty + 1, 4);
+    mbar_init(acc_empty + 0, 4 * kTcQT);  // the warps of the kTcQT warpgroups of a buffer
+    mbar_init(acc_empty + 1, 4 * kTcQT);
+    for (int i = 0; i < kNormRing; ++i) mbar_init(n_full + i, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) {  // two accumulators of 128 columns
+  if (warp == 1) {  // 2 buffers x kTcQT query tiles x 128 columns = all 512
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(sh_u32(tmem_slot)), "r"(2 * kTcN)
+                 ::"r"(sh_u32(tmem_slot)), "r"(2 * kTcQT * kTcN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -370,9 +418,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- TMA producer
     asm volatile("prefetch.tensormap [%0];" ::"l"(&qmap) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&xmap) : "memory");
-    mbar_expect_tx(a_full, natoms * kAtomBytes);
-    for (int at = 0; at < natoms; ++at)
-      tma_load_2d(sA + at * kAtomBytes, &qmap, a_full, 64 * at, static_cast<int>(q0));
+    mbar_expect_tx(a_full, kTcQT * natoms * kAtomBytes);
+    for (int qt = 0; qt < kTcQT; ++qt)
+      for (int at = 0; at < natoms; ++at)
+        tma_load_2d(sA + (qt * 2 + at) * kAtomBytes, &qmap, a_full, 64 * at,
+                    static_cast<int>(q0 + qt * kTcM));
     int issued = 0;
     bool ok = true;
     for (int i = 0; i < my_tiles && ok; ++i) {
@@ -383,6 +433,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int row = (t_lo + i) * kTcN;
       for (int at = 0; at < natoms; ++at)
         tma_load_2d(sB + (st * 2 + at) * kAtomBytes, &xmap, full + st, 64 * at, row);
+      // the tile's 128 base norms.  Slot i % kNormRing was last read by the
+      // epilogue of tile i - kNormRing, which finished before the MMA of
+      // tile i - kTcStages - 2 began, and that MMA completed before stage
+      // i % kTcStages came free above.
+      const int ns = i % kNormRing;
+      mbar_expect_tx(n_full + ns, kTcN * 4);
+      bulk_load(sN + ns * kTcN, a.xn + row, kTcN * 4, n_full + ns);
       issued = i + 1;
     }
     if (!ok) {
@@ -390,6 +447,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_drain(a_full, 0);
       for (int i = issued - kTcStages < 0 ? 0 : issued - kTcStages; i < issued; ++i)
         mbar_drain(full + (i % kTcStages), (i / kTcStages) & 1);
+      for (int i = issued - kNormRing < 0 ? 0 : issued - kNormRing; i < issued; ++i)
+        mbar_drain(n_full + (i % kNormRing), (i / kNormRing) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
@@ -405,86 +464,145 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!mbar_wait(full + st, ph, abort)) break;
         tc_fence_after();
         const uint32_t b_base = sh_u32(sB + st * 2 * kAtomBytes);
-        const uint32_t d_tmem = tmem + static_cast<uint32_t>(b * kTcN);
-        for (int at = 0; at < natoms; ++at)
+        for (int qt = 0; qt < kTcQT; ++qt) {
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>((b * kTcQT + qt) * kTcN);
+          const uint32_t aq = a_base + static_cast<uint32_t>(qt * 2 * kAtomBytes);
+          for (int at = 0; at < natoms; ++at)
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            // a 16-coordinate step inside a 128-byte swizzled row is 32 bytes
-            const uint64_t ad = sw128_desc(a_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
-            const uint64_t bd = sw128_desc(b_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
-            tc_mma(d_tmem, ad, bd, (at | kk) != 0);
-          }
+            for (int kk = 0; kk < 4; ++kk) {
+              // a 16-coordinate step inside a 128-byte swizzled row is 32 bytes
+              const uint64_t ad = sw128_desc(aq + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
+              const uint64_t bd = sw128_desc(b_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
+              tc_mma(d_tmem, ad, bd, (at | kk) != 0);
+            }
+        }
         tc_commit(empty + st);
         tc_commit(acc_full + b);
       }
     }
   } else if (warp >= 4) {
     // ---- epilogue: one query per thread, its running top-k in local memory
-    const int e = (warp - 4) >> 2;  // warpgroup = accumulator
-    const int quarter = warp & 3;
-    const int row = quarter * 32 + lane;
-    const int64_t gq = q0 + row;
+    const int wg = (warp - 4) >> 2;
+    const int qt = wg % kTcQT;      // query tile
+    const int b = wg / kTcQT;       // accumulator buffer = tiles b, b+2, ...
+    const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. +31
+    const int64_t gq = q0 + qt * kTcM + quarter * 32 + lane;
     const bool live = gq < a.nq;
     const float qn = live ? __ldg(a.qn + gq) : 0.f;
     const int k = a.k;
     unsigned long long top[kMaxK];
     int have = 0;
-    unsigned long long thr = ~0ull;
-    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
-    for (int i = e; i < my_tiles; i += 2) {
-      const uint32_t u = static_cast<uint32_t>(i >> 1);
-      // one lane waits, so the warp stays converged for tcgen05.ld
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait(acc_full + e, u & 1u, abort) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      tc_fence_after();
-      const int col0 = (t_lo + i) * kTcN;
-#pragma unroll 1
-      for (int c = 0; c < kTcN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + lane_base + static_cast<uint32_t>(e * kTcN + c * 32), r);
-        const int j0 = col0 + c * 32;
-        // the 32 base norms of this chunk: one coalesced load, then shuffles
-        const float xv = (j0 + lane < a.chunk_n) ? __ldg(a.xn + j0 + lane) : 0.f;
-        const unsigned thr_d = static_cast<unsigned>(thr >> 32);
-        // pass 1, converged: every distance, and the mask of the columns at
-        // or below this query's k-th best so far
-        unsigned cm = 0u;
+    // Bounds on the keys that can still enter the final top-k: the running
+    // k-th best of the chunks folded so far (keys are distinct: ids differ),
+    // and the shared per-query distance bound, which every CTA lowers to its
+    // own k-th distance (k keys of one range at or below it mean no key
+    // above it is in the final k).  thr_f is the same bound on
+    // v = |x|^2 - 2 q.x; a row past the query count never qualifies.
+    unsigned long long thr =
+        live ? a.keys[static_cast<size_t>(gq) * a.nslots * k + (k - 1)] : 0ull;
+    float thr_f = !live ? -FLT_MAX
+                        : (thr == ~0ull ? FLT_MAX : static_cast<float>(static_cast<unsigned>(thr >> 32)) - qn);
+    unsigned published = ~0u;  // the last distance this thread lowered the shared bound to
+    auto tighten = [&](unsigned dist) {
+      const unsigned long long kb = (static_cast<unsigned long long>(dist) << 32) | 0xffffffffull;
+      if (kb < thr) {
+        thr = kb;
+        thr_f = static_cast<float>(dist) - qn;
+      }
+    };
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                           static_cast<uint32_t>((b * kTcQT + qt) * kTcN);
+
+    // 32 columns: v = |x|^2 - 2 q.x, a tree of 3-input mins, and only if the
+    // minimum is within the bound, the lane's candidates one by one
+    auto scan = [&](const uint32_t (&r)[32], const float* nrm, int j0) {
+      float v[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float x = __shfl_sync(0xffffffffu, xv, j);
-          r[j] = static_cast<unsigned>(fmaf(-2.f, __uint_as_float(r[j]), qn + x));
-          cm |= static_cast<unsigned>(r[j] <= thr_d && j0 + j < a.chunk_n) << j;
+      for (int g = 0; g < 8; ++g) {
+        const float4 nv = reinterpret_cast<const float4*>(nrm)[g];
+        v[4 * g + 0] = fmaf(-2.f, __uint_as_float(r[4 * g + 0]), nv.x);
+        v[4 * g + 1] = fmaf(-2.f, __uint_as_float(r[4 * g + 1]), nv.y);
+        v[4 * g + 2] = fmaf(-2.f, __uint_as_float(r[4 * g + 2]), nv.z);
+        v[4 * g + 3] = fmaf(-2.f, __uint_as_float(r[4 * g + 3]), nv.w);
+      }
+      float p[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) p[g] = min3f(v[4 * g], v[4 * g + 1], fminf(v[4 * g + 2], v[4 * g + 3]));
+      const float m = min3f(min3f(p[0], p[1], p[2]), min3f(p[3], p[4], p[5]), fminf(p[6], p[7]));
+      if (m > thr_f) return;  // the common case: nothing within the bound
+      unsigned cm = 0u;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) cm |= static_cast<unsigned>(v[j] <= thr_f) << j;
+      float dl[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) dl[j] = v[j];
+      while (cm) {
+        const int j = __ffs(cm) - 1;
+        cm &= cm - 1u;
+        if (dl[j] > thr_f) continue;  // the bound tightened after the mask was taken
+        // v and |q|^2 are integers below 2^24: the sum is the exact distance
+        const unsigned dist = __float2uint_rn(dl[j] + qn);
+        const unsigned long long key =
+            (static_cast<unsigned long long>(dist) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
+        if (key >= thr) continue;
+        int pos = have < k ? have : k - 1;
+        while (pos > 0 && top[pos - 1] > key) {
+          top[pos] = top[pos - 1];
+          --pos;
         }
-        if (!live || cm == 0u) continue;  // the common case: nothing below the k-th
-        // pass 2, this lane only: its few candidates, through a local copy
-        unsigned dl[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) dl[j] = r[j];
-        while (cm) {
-          const int j = __ffs(cm) - 1;
-          cm &= cm - 1u;
-          const unsigned long long key =
-              (static_cast<unsigned long long>(dl[j]) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
-          if (key < thr) {
-            int p = have < k ? have : k - 1;
-            while (p > 0 && top[p - 1] > key) {
-              top[p] = top[p - 1];
-              --p;
-            }
-            top[p] = key;
-            if (have < k) ++have;
-            if (have == k) thr = top[k - 1];
+        top[pos] = key;
+        if (have < k) ++have;
+        if (have == k) {
+          const unsigned long long kth = top[k - 1];
+          if (kth < thr) {
+            thr = kth;
+            thr_f = static_cast<float>(static_cast<unsigned>(kth >> 32)) - qn;
+          }
+          const unsigned kd = static_cast<unsigned>(kth >> 32);
+          if (kd < published) {
+            atomicMin(a.bound + gq, kd);
+            published = kd;
           }
         }
       }
+    };
+
+    for (int i = b; i < my_tiles; i += 2) {
+      const uint32_t u = static_cast<uint32_t>(i >> 1);
+      const int ns = i % kNormRing;
+      // one lane waits, so the warp stays converged for tcgen05.ld
+      int ok = 1;
+      if (lane == 0)
+        ok = (mbar_wait(acc_full + b, u & 1u, abort) &&
+              mbar_wait(n_full + ns, static_cast<uint32_t>(i / kNormRing) & 1u, abort)) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      tc_fence_after();
+      if (live) tighten(__ldcg(a.bound + gq));
+      const int col0 = (t_lo + i) * kTcN;
+      const float* nrm = sN + ns * kTcN;
+      // the next 32 columns load while the current ones are scanned; the
+      // accumulator goes back to the MMA once its last columns are in
+      // registers
+      uint32_t r0[32], r1[32];
+      tmem_ld32_async(taddr, r0);
+      tmem_wait(r0);
+      tmem_ld32_async(taddr + 32u, r1);
+      scan(r0, nrm, col0);
+      tmem_wait(r1);
+      tmem_ld32_async(taddr + 64u, r0);
+      scan(r1, nrm + 32, col0 + 32);
+      tmem_wait(r0);
+      tmem_ld32_async(taddr + 96u, r1);
+      scan(r0, nrm + 64, col0 + 64);
+      tmem_wait(r1);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty + e);
+      if (lane == 0) mbar_arrive(acc_empty + b);
+      scan(r1, nrm + 96, col0 + 96);
     }
     if (live) {
       unsigned long long* out =
-          a.keys + (static_cast<size_t>(gq) * a.nslots + 1 + 2 * s + e) * static_cast<size_t>(k);
+          a.keys + (static_cast<size_t>(gq) * a.nslots + 1 + 2 * s + b) * static_cast<size_t>(k);
       for (int j = 0; j < k; ++j) out[j] = j < have ? top[j] : ~0ull;
     }
   }
@@ -494,28 +612,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0 && *abort) atomicExch(a.error, 1);
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcQT * kTcN)
                  : "memory");
   }
 }
 
 // uint8 rows -> BF16 rows zero-padded to dp coordinates, and each row's
-// squared norm (an exact integer in FP32).  One warp per row.
-__global__ void to_bf16_rows(const uint8_t* __restrict__ x, int64_t rows, int d, int dp,
+// squared norm (an exact integer in FP32).  Rows in [rows, rows_pad) are
+// zero with norm +inf.  One warp per row.
+__global__ void to_bf16_rows(const uint8_t* __restrict__ x, int64_t rows, int64_t rows_pad, int d, int dp,
                              uint16_t* __restrict__ out, float* __restrict__ norms) {
   const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
-  const uint8_t* src = x + r * d;
+  if (r >= rows_pad) return;
+  const bool real = r < rows;
+  const uint8_t* src = x + (real ? r : 0) * d;
   uint16_t* dst = out + r * dp;
   unsigned sq = 0;
   for (int j = lane; j < dp; j += 32) {
-    const unsigned v = j < d ? src[j] : 0u;
+    const unsigned v = (real && j < d) ? src[j] : 0u;
     sq += v * v;
     dst[j] = static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);  // exact
   }
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if (lane == 0) norms[r] = static_cast<float>(sq);
+  if (lane == 0) norms[r] = real ? static_cast<float>(sq) : __int_as_float(0x7f800000);
 }
 
 // Merge the parts of every query into its running top-k (slot 0) and clear
@@ -568,7 +688,8 @@ bool bf16_row_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr size_t kTcSmem = 1024 + 2 * kAtomBytes + kTcStages * 2 * kAtomBytes + 256;
+constexpr size_t kTcSmem =
+    1024 + kTcQT * 2 * kAtomBytes + kTcStages * 2 * kAtomBytes + kNormRing * kTcN * 4 + 256;
 
 }  // namespace
 
@@ -583,49 +704,61 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
   const int dp = d <= 64 ? 64 : 128;
   const int natoms = dp / 64;
   const int64_t chunk = n < (1ll << 22) ? n : (1ll << 22);
-  const int64_t qtiles = (nq + kTcM - 1) / kTcM;
+  const int64_t qblocks = (nq + kTcQT * kTcM - 1) / (kTcQT * kTcM);
   const int max_tiles = static_cast<int>((chunk + kTcN - 1) / kTcN);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // enough CTAs for a few waves of one CTA per SM, each over >= 8 tiles
-  int splits = static_cast<int>((4ll * sms + qtiles - 1) / qtiles);
-  if (splits > max_tiles / 8) splits = max_tiles / 8;
-  if (splits < 1) splits = 1;
+  // CTAs (one per SM at a time): at least four waves, each CTA over >= 8
+  // tiles, and among up to 4x the least such count the one that fills its
+  // last wave best
+  const int s_lo = static_cast<int>((4ll * sms + qblocks - 1) / qblocks);
+  const int s_hi = max_tiles / 8 < 1 ? 1 : max_tiles / 8;
+  int splits = s_lo < s_hi ? s_lo : s_hi;
+  double best_fill = -1.0;
+  for (int sp = splits; sp <= s_hi && sp <= 4 * s_lo; ++sp) {
+    const int64_t ctas = qblocks * sp;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    const double fill = static_cast<double>(ctas) / static_cast<double>(waves * sms);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      splits = sp;
+    }
+  }
   const int nslots = 1 + 2 * splits;
   uint16_t *qb = nullptr, *xb = nullptr;
   float *qn = nullptr, *xn = nullptr;
   unsigned long long* keys = nullptr;
+  unsigned* bound = nullptr;
   int* err = nullptr;
-  // row buffers hold at least one full 128-row box (zero rows past the data)
-  const int64_t q_rows = nq > kTcM ? nq : kTcM;
-  const int64_t x_rows = chunk > kTcN ? chunk : kTcN;
+  // row buffers padded to whole boxes (zero rows, +inf norms), so every TMA
+  // box lies inside its buffer
+  const int64_t q_rows = qblocks * kTcQT * kTcM;
+  const int64_t x_rows = static_cast<int64_t>(max_tiles) * kTcN;
   cudaError_t e = cudaMalloc(&qb, static_cast<size_t>(q_rows) * dp * 2);
-  if (e == cudaSuccess) e = cudaMemsetAsync(qb, 0, static_cast<size_t>(q_rows) * dp * 2, stream);
-  if (e == cudaSuccess) e = cudaMalloc(&qn, static_cast<size_t>(nq) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&qn, static_cast<size_t>(q_rows) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&xb, static_cast<size_t>(x_rows) * dp * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&xn, static_cast<size_t>(chunk) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&xn, static_cast<size_t>(x_rows) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&keys, static_cast<size_t>(nq) * nslots * k * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&bound, static_cast<size_t>(nq) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bound, 0xff, static_cast<size_t>(nq) * 4, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, static_cast<size_t>(nq) * nslots * k * 8, stream);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTcSmem));
   CUtensorMap qmap, xmap;
   if (e == cudaSuccess) {
-    to_bf16_rows<<<static_cast<unsigned>((nq * 32 + 255) / 256), 256, 0, stream>>>(queries, nq, d, dp, qb, qn);
+    to_bf16_rows<<<static_cast<unsigned>((q_rows * 32 + 255) / 256), 256, 0, stream>>>(queries, nq, q_rows, d, dp,
+                                                                                     qb, qn);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && !bf16_row_map(&qmap, qb, q_rows, dp)) e = cudaErrorInvalidValue;
   for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
     const int64_t cn = (n - c0 < chunk) ? n - c0 : chunk;
-    const int64_t map_rows = cn > kTcN ? cn : kTcN;
-    if (cn < kTcN) {
-      e = cudaMemsetAsync(xb + cn * dp, 0, static_cast<size_t>(kTcN - cn) * dp * 2, stream);
-      if (e != cudaSuccess) break;
-    }
-    to_bf16_rows<<<static_cast<unsigned>((cn * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn, d, dp,
-                                                                                 xb, xn);
+    const int64_t map_rows = (cn + kTcN - 1) / kTcN * kTcN;
+    to_bf16_rows<<<static_cast<unsigned>((map_rows * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn,
+                                                                                       map_rows, d, dp, xb, xn);
     if (!bf16_row_map(&xmap, xb, map_rows, dp)) {
       e = cudaErrorInvalidValue;
       break;
@@ -634,7 +767,6 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
     ta.qn = qn;
     ta.xn = xn;
     ta.nq = nq;
-    ta.chunk_n = static_cast<int32_t>(cn);
     ta.id0 = c0;
     ta.tiles = static_cast<int32_t>((cn + kTcN - 1) / kTcN);
     ta.splits = splits < ta.tiles ? splits : ta.tiles;
@@ -642,8 +774,9 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
     ta.k = k;
     ta.nslots = nslots;
     ta.keys = keys;
+    ta.bound = bound;
     ta.error = err;
-    knn_tc_kernel<<<dim3(static_cast<unsigned>(qtiles), static_cast<unsigned>(ta.splits)), kTcThreads, kTcSmem,
+    knn_tc_kernel<<<dim3(static_cast<unsigned>(qblocks), static_cast<unsigned>(ta.splits)), kTcThreads, kTcSmem,
                     stream>>>(qmap, xmap, ta);
     topk_fold<<<static_cast<unsigned>(nq), 256, 0, stream>>>(keys, nslots, k);
     e = cudaGetLastError();
@@ -662,6 +795,7 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
   cudaFree(xb);
   cudaFree(xn);
   cudaFree(keys);
+  cudaFree(bound);
   cudaFree(err);
   return e;
 }
