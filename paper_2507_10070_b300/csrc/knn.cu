@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 // the end never qualify.  The bound starts at the running k-th best of the
 // chunks already folded, and the CTAs of a query share a distance bound in
 // global memory: each lowers it (atomicMin) to its own k-th distance and
-// reads it once per tile, so a CTA's first tiles no longer admit a stream of
-// candidates that another CTA has already ruled out.
+// reads it once per tile (a tile ahead), so a CTA's first tiles no longer
+// admit a stream of candidates that another CTA has already ruled out.
 // Each warpgroup writes its lists as one part; a fold kernel merges the parts
 // with the running top-k after each chunk of the base.
 // Every wait on an mbarrier is bounded: past ~2 s the CTA sets an abort flag,
@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 constexpr int kTcM = 128;            // queries per CTA (MMA M)
 constexpr int kTcN = 128;            // base rows per tile (MMA N)
 constexpr int kTcQT = 2;             // query tiles per CTA
-constexpr int kTcStages = 4;         // base-tile ring
+constexpr int kTcStages = 3;         // base-tile ring
 constexpr int kNormRing = 8;         // base-norm slots (one tile each)
+static_assert(kNormRing >= kTcStages + 2, "a norm slot is reused only after its tile's epilogue");
 constexpr int kAtomBytes = 128 * 128;  // one 64-coordinate BF16 atom of a 128-row tile
 constexpr int kTcThreads = 128 + 4 * 128;
 constexpr long long kTcWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -247,13 +248,29 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// As mbar_test, but the thread may sleep in the instruction until the phase
+// completes or about `ns` nanoseconds pass, instead of spinning on issue
+// slots that the epilogue warps of the same SM sub-partition need.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(sh_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr uint32_t kTcSleepNs = 20000;
+
 // Wait for the phase of `bar` with this parity; false if the CTA aborted or
 // the wait ran out (which aborts it).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   const long long t0 = clock64();
   for (uint32_t i = 0;; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if ((i & 63u) == 63u) {
+    if (mbar_test_sleep(bar, parity, kTcSleepNs)) return true;
+    if ((i & 15u) == 15u) {
       if (*abort) return false;
       if (clock64() - t0 > kTcWaitCycles) {
         *abort = 1;
@@ -435,8 +452,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tma_load_2d(sB + (st * 2 + at) * kAtomBytes, &xmap, full + st, 64 * at, row);
       // the tile's 128 base norms.  Slot i % kNormRing was last read by the
       // epilogue of tile i - kNormRing, which finished before the MMA of
-      // tile i - kTcStages - 2 began, and that MMA completed before stage
-      // i % kTcStages came free above.
+      // tile i - kNormRing + 2 began; that MMA is at or before the MMA of
+      // tile i - kTcStages, whose completion freed the stage above.
       const int ns = i % kNormRing;
       mbar_expect_tx(n_full + ns, kTcN * 4);
       bulk_load(sN + ns * kTcN, a.xn + row, kTcN * 4, n_full + ns);
@@ -533,15 +550,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       unsigned cm = 0u;
 #pragma unroll
       for (int j = 0; j < 32; ++j) cm |= static_cast<unsigned>(v[j] <= thr_f) << j;
-      float dl[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) dl[j] = v[j];
       while (cm) {
         const int j = __ffs(cm) - 1;
         cm &= cm - 1u;
-        if (dl[j] > thr_f) continue;  // the bound tightened after the mask was taken
+        // v[j] for a run-time j without local memory: a select tree on j's bits
+        float t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+        for (int x = 0; x < 16; ++x) t16[x] = (j & 1) ? v[2 * x + 1] : v[2 * x];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) t8[x] = (j & 2) ? t16[2 * x + 1] : t16[2 * x];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) t4[x] = (j & 4) ? t8[2 * x + 1] : t8[2 * x];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) t2[x] = (j & 8) ? t4[2 * x + 1] : t4[2 * x];
+        const float vj = (j & 16) ? t2[1] : t2[0];
+        if (vj > thr_f) continue;  // the bound tightened after the mask was taken
         // v and |q|^2 are integers below 2^24: the sum is the exact distance
-        const unsigned dist = __float2uint_rn(dl[j] + qn);
+        const unsigned dist = __float2uint_rn(vj + qn);
         const unsigned long long key =
             (static_cast<unsigned long long>(dist) << 32) | static_cast<unsigned>(a.id0 + j0 + j);
         if (key >= thr) continue;
@@ -567,6 +592,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     };
 
+    // the shared bound is read one tile ahead, off the critical path
+    unsigned next_bound = live ? __ldcg(a.bound + gq) : ~0u;
     for (int i = b; i < my_tiles; i += 2) {
       const uint32_t u = static_cast<uint32_t>(i >> 1);
       const int ns = i % kNormRing;
@@ -577,7 +604,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               mbar_wait(n_full + ns, static_cast<uint32_t>(i / kNormRing) & 1u, abort)) ? 1 : 0;
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       tc_fence_after();
-      if (live) tighten(__ldcg(a.bound + gq));
+      if (live) {
+        tighten(next_bound);
+        next_bound = __ldcg(a.bound + gq);
+      }
       const int col0 = (t_lo + i) * kTcN;
       const float* nrm = sN + ns * kTcN;
       // the next 32 columns load while the current ones are scanned; the
