@@ -430,15 +430,30 @@ int ann_autotune_degree(const ann_autotune_cfg* cfg, ann_autotune_point* points,
 /*
  * The same Vamana construction on the GPU (index-build tooling): the batch
  * searches run on the library's search kernel (exact navigation on the
- * vectors in HBM), RobustPrune runs one warp per node, and back edges are
- * grouped by a device sort.  The candidate pool of a node is the L_build
- * expanded nodes nearest to it.  Deterministic.  Needs d % 16 == 0,
- * 1 <= R <= 128, R <= L_build <= 256 - R.  Uses the current device; host
- * buffers in and out, as ann_build_graph.
+ * vectors in HBM), and back edges are grouped by a device sort.
+ * RobustPrune (Section "Background", Vamana) takes the distances between a
+ * node's candidates from the tensor cores for uint8 rows with d <= 128
+ * (BF16 MMAs with FP32 accumulation, exact for 8-bit integers), and from
+ * one warp of CUDA cores per node otherwise; both make the same decisions.
+ * The candidate pool of a node is the L_build expanded nodes nearest to it.
+ * Deterministic.  Needs d % 16 == 0, 1 <= R <= 128, R <= L_build <= 256 - R.
+ * Uses the current device; host buffers in and out, as ann_build_graph.
  */
 int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
                         float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
                         int32_t* entry_out);
+
+/* Engines of ann_build_graph_gpu_ex (where RobustPrune's distances run). */
+typedef enum {
+  ANN_BUILD_AUTO = 0,         /* tensor cores where the data allow, else CUDA cores */
+  ANN_BUILD_TENSOR_CORES = 1, /* uint8 data with d <= 128 only (ANN_EINVAL otherwise) */
+  ANN_BUILD_CUDA_CORES = 2    /* one warp per node on the CUDA cores */
+} ann_build_engine;
+
+/* ann_build_graph_gpu with an engine choice; the graph does not depend on it. */
+int ann_build_graph_gpu_ex(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                           float alpha, int32_t L_build, uint64_t seed, int32_t engine,
+                           int32_t* adj_out, int32_t* entry_out);
 
 /*
  * Compressed navigation vectors (host-side encoders).  The precision

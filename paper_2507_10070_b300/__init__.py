@@ -291,17 +291,22 @@ def build_pq(base, M: int, n_train: int = 100_000, iters: int = 25, kpp_uniforms
 
 
 def build_graph(base, R: int, alpha: float = 1.2, L_build: int = 128, seed: int = 0,
-                threads: int = 0, device: str = "cpu"):
+                threads: int = 0, device: str = "cpu", engine: str = "auto"):
     """Vamana graph on host threads (device="cpu") or on the GPU
-    (device="gpu").  Returns (adj int32 (n,R), entry)."""
+    (device="gpu").  On the GPU, engine chooses where RobustPrune's candidate
+    distances run: "auto" (tensor cores for uint8 data with d <= 128, else
+    CUDA cores), "tensor" or "cuda"; the graph is the same.  Returns
+    (adj int32 (n,R), entry)."""
     base = _c(base)
     n, d = base.shape
     adj = np.empty((n, R), np.int32)
     entry = ctypes.c_int32(0)
     if device == "gpu":
-        _check(_lib().ann_build_graph_gpu(_p(base), _dtype_code(base), n, d, R,
-                                          ctypes.c_float(alpha), L_build, ctypes.c_uint64(seed),
-                                          _p(adj), ctypes.byref(entry)))
+        eng = {"auto": _abi.ANN_BUILD_AUTO, "tensor": _abi.ANN_BUILD_TENSOR_CORES,
+               "cuda": _abi.ANN_BUILD_CUDA_CORES}[engine]
+        _check(_lib().ann_build_graph_gpu_ex(_p(base), _dtype_code(base), n, d, R,
+                                             ctypes.c_float(alpha), L_build, ctypes.c_uint64(seed), eng,
+                                             _p(adj), ctypes.byref(entry)))
     else:
         _check(_lib().ann_build_graph(_p(base), _dtype_code(base), n, d, R, ctypes.c_float(alpha),
                                       L_build, ctypes.c_uint64(seed), threads, _p(adj),

@@ -13,6 +13,7 @@ ANN_TIER_HOST_PINNED, ANN_TIER_HBM = 0, 1
 ANN_NAV_AUTO, ANN_NAV_BF16, ANN_NAV_FP8 = 0, 1, 2
 
 ANN_KNN_AUTO, ANN_KNN_TENSOR_CORES, ANN_KNN_CUDA_CORES = 0, 1, 2
+ANN_BUILD_AUTO, ANN_BUILD_TENSOR_CORES, ANN_BUILD_CUDA_CORES = 0, 1, 2
 
 STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA",
                 -4: "ANN_ETIMEOUT", -5: "ANN_EBUSY", -6: "ANN_EIO"}
@@ -26,7 +27,8 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_knn_exact_ex", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
-           "ann_autotune_degree", "ann_build_graph_gpu", "ann_encode_bf16", "ann_encode_fp8e4m3",
+           "ann_autotune_degree", "ann_build_graph_gpu", "ann_build_graph_gpu_ex", "ann_encode_bf16",
+           "ann_encode_fp8e4m3",
            "ann_pq_encode_gpu", "ann_reorder_graph"]
 
 
@@ -133,6 +135,9 @@ def lib():
         L.ann_build_graph_gpu.restype = ctypes.c_int
         L.ann_build_graph_gpu.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, P,
                                           ctypes.POINTER(ctypes.c_int32)]
+        L.ann_build_graph_gpu_ex.restype = ctypes.c_int
+        L.ann_build_graph_gpu_ex.argtypes = [P, I32, I64, I32, I32, ctypes.c_float, I32, U64, I32, P,
+                                             ctypes.POINTER(ctypes.c_int32)]
         L.ann_encode_bf16.restype = ctypes.c_int
         L.ann_encode_bf16.argtypes = [P, I64, P]
         L.ann_encode_fp8e4m3.restype = ctypes.c_int

@@ -15,10 +15,12 @@
 //     depth 0); the expanded nodes nearest to x_p, up to L_build + 64 (at
 //     most 256 - R), form the candidate pool -- in practice the whole
 //     expanded set, as in DiskANN;
-//  3. RobustPrune(p, pool u N(p)) -- one warp per node (prune_kernel);
+//  3. RobustPrune(p, pool u N(p)) -- for uint8 rows with d <= 128 one block
+//     per node with the candidate distances on the tensor cores
+//     (prune_tc_kernel), otherwise one warp per node (prune_kernel);
 //  4. back edges j <- p: the (j, p) pairs are sorted on the device (CUB
 //     radix sort), grouped by j, and each target appends its new sources or,
-//     if they do not fit in R, prunes N(j) u sources (prune_kernel again).
+//     if they do not fit in R, prunes N(j) u sources (the prune again).
 // alpha is compared with squared distances (DiskANN's convention).  Every
 // step is deterministic, so the graph does not depend on timing.
 #include <cub/cub.cuh>
@@ -167,10 +169,14 @@ __global__ void prune_kernel(const void* __restrict__ base, int d, int R, float 
     K[c] = key;
   }
   __syncwarp();
-  // sort 256 keys (bitonic, shared memory, 8 compare-exchanges per lane per stage)
-  for (int size = 2; size <= kCandMax; size <<= 1) {
+  // sort the keys (bitonic, shared memory): only the first P, the least
+  // power of two >= the candidate count, since every later key is the ~0
+  // sentinel and already in place
+  int P = 32;
+  while (P < nc) P <<= 1;
+  for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = lane; i < kCandMax; i += 32) {
+      for (int i = lane; i < P; i += 32) {
         const int j = i ^ stride;
         if (j > i) {
           const bool asc = (i & size) == 0;
@@ -215,6 +221,285 @@ __global__ void prune_kernel(const void* __restrict__ base, int d, int R, float 
   }
   __syncwarp();
   for (int j = kept + lane; j < adj_stride; j += 32) row[j] = -1;
+}
+
+// RobustPrune for uint8 rows with d <= 128 with the candidate distances on the
+// tensor cores.  One block of four warps per task.
+//  1. The candidates' rows are staged in shared memory as BF16 (exact for
+//     8-bit values), with each row's squared norm and its exact integer
+//     distance to p (8 threads per row, __vabsdiffu4 + __dp4a).
+//  2. (distance to p, id) keys are sorted (bitonic, 256 entries) and
+//     deduplicated into the unique candidates in prune order.
+//  3. If the task may append and they fit in R, they become the row.
+//     Otherwise every pair i < j of them gets d(c_i, c_j) = |c_i|^2 +
+//     |c_j|^2 - 2 c_i.c_j from BF16 MMAs with FP32 accumulation
+//     (mma.sync m16n8k16).  For uint8 rows with d <= 128 every partial sum is
+//     an integer below 2^24, so this is exact in any order.  The result is
+//     a bit matrix B[i][j] = (alpha * d(c_i, c_j) <= d(p, c_j)).
+//  4. One warp walks the candidates in order: a candidate not yet pruned is
+//     kept, and its row of B prunes the later ones, until R are kept.
+// Every comparison is the one prune_kernel<true> makes, on the same exact
+// float values, so both give the same rows.
+constexpr int kTcPruneStride = 136;  // BF16 elements per staged row: 128 + 8 (bank spread)
+constexpr int kTcPruneThreads = 128;
+constexpr size_t kTcPruneSmem = (size_t)(kCandMax + 1) * kTcPruneStride * 2  // rows + one zero row
+                                + kCandMax * 8                               // keys
+                                + kCandMax * 4 * 2                           // norms, ids
+                                + kCandMax * 2                               // sorted -> slot, unique -> sorted
+                                + kCandMax * 32                              // bit matrix
+                                + 16;
+
+__device__ __forceinline__ uint32_t bf16x2_of_bytes(uint32_t w, int hi) {
+  // bytes 2*hi and 2*hi+1 of w as two BF16 values (exact: 8-bit integers)
+  const uint32_t b0 = (w >> (16 * hi)) & 0xffu, b1 = (w >> (16 * hi + 8)) & 0xffu;
+  const uint32_t h0 = __float_as_uint(static_cast<float>(b0)) >> 16;
+  const uint32_t h1 = __float_as_uint(static_cast<float>(b1)) >> 16;
+  return h0 | (h1 << 16);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(kTcPruneThreads)
+    prune_tc_kernel(const uint8_t* __restrict__ base, int d, int R, float alpha,
+                    const int32_t* __restrict__ task_node, const int32_t* __restrict__ extra,
+                    const int64_t* __restrict__ extra_off, const int32_t* __restrict__ extra_cnt,
+                    int include_row, int append_if_fits, int32_t* __restrict__ adj, int adj_stride) {
+  extern __shared__ __align__(16) unsigned char prune_smem[];
+  uint16_t* X = reinterpret_cast<uint16_t*>(prune_smem);                        // [257][136] BF16
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(X + (kCandMax + 1) * kTcPruneStride);
+  float* nrm = reinterpret_cast<float*>(K + kCandMax);                          // |x|^2 by slot
+  int32_t* cid = reinterpret_cast<int32_t*>(nrm + kCandMax);                    // id by slot (-1: none)
+  uint8_t* slot = reinterpret_cast<uint8_t*>(cid + kCandMax);                   // sorted position -> slot
+  uint8_t* U = slot + kCandMax;                                                 // unique position -> sorted
+  uint32_t* bits = reinterpret_cast<uint32_t*>(U + kCandMax);                   // [256][8]
+  int* misc = reinterpret_cast<int*>(bits + kCandMax * 8);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int task = blockIdx.x;
+  const int p = task_node[task];
+  int32_t* row = adj + (size_t)p * adj_stride;
+  if (tid == 0) {
+    int nrow = 0;
+    if (include_row)
+      while (nrow < R && row[nrow] >= 0) ++nrow;
+    misc[0] = nrow;
+  }
+  __syncthreads();
+  const int nrow = misc[0];
+  const int ne = min(extra_cnt[task], kCandMax - nrow);
+  const int32_t* ex = extra + extra_off[task];
+  const int nc = nrow + ne;
+  for (int c = tid; c < kCandMax; c += kTcPruneThreads) {
+    int id = -1;
+    if (c < nc) {
+      id = c < nrow ? row[c] : ex[c - nrow];
+      if (id == p) id = -1;
+    }
+    cid[c] = id;
+    slot[c] = static_cast<uint8_t>(c);
+  }
+  // the zero row that fills MMA tiles past the last candidate
+  for (int j = tid; j < kTcPruneStride / 2; j += kTcPruneThreads)
+    reinterpret_cast<uint32_t*>(X + kCandMax * kTcPruneStride)[j] = 0u;
+  __syncthreads();
+
+  // 1. stage rows, norms and exact distances to p: 8 threads per row, 16
+  // coordinates each
+  const int segs = d >> 4, sub = tid & 7, grp = tid >> 3;
+  uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+  if (sub < segs) pv = __ldg(reinterpret_cast<const uint4*>(base + (size_t)p * d) + sub);
+  constexpr int kRowsPerPass = kTcPruneThreads / 8;
+  constexpr int kBatch = 8;  // row loads a thread has in flight at once
+  for (int c00 = 0; c00 < kCandMax; c00 += kRowsPerPass * kBatch) {
+    uint4 vb[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int id = cid[c00 + u * kRowsPerPass + grp];
+      vb[u] = (id >= 0 && sub < segs) ? __ldg(reinterpret_cast<const uint4*>(base + (size_t)id * d) + sub)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int c = c00 + u * kRowsPerPass + grp;
+      const int id = cid[c];
+      const uint4 v = vb[u];
+      unsigned nn = 0, dd = 0, t;
+      nn = __dp4a(v.x, v.x, nn);
+      nn = __dp4a(v.y, v.y, nn);
+      nn = __dp4a(v.z, v.z, nn);
+      nn = __dp4a(v.w, v.w, nn);
+      t = __vabsdiffu4(v.x, pv.x); dd = __dp4a(t, t, dd);
+      t = __vabsdiffu4(v.y, pv.y); dd = __dp4a(t, t, dd);
+      t = __vabsdiffu4(v.z, pv.z); dd = __dp4a(t, t, dd);
+      t = __vabsdiffu4(v.w, pv.w); dd = __dp4a(t, t, dd);
+      if (sub < segs) {
+        uint4 w0, w1;
+        w0.x = bf16x2_of_bytes(v.x, 0); w0.y = bf16x2_of_bytes(v.x, 1);
+        w0.z = bf16x2_of_bytes(v.y, 0); w0.w = bf16x2_of_bytes(v.y, 1);
+        w1.x = bf16x2_of_bytes(v.z, 0); w1.y = bf16x2_of_bytes(v.z, 1);
+        w1.z = bf16x2_of_bytes(v.w, 0); w1.w = bf16x2_of_bytes(v.w, 1);
+        uint4* dst = reinterpret_cast<uint4*>(X + c * kTcPruneStride + sub * 16);
+        dst[0] = w0;
+        dst[1] = w1;
+      }
+      for (int o = 1; o < 8; o <<= 1) {
+        nn += __shfl_xor_sync(kFull, nn, o);
+        dd += __shfl_xor_sync(kFull, dd, o);
+      }
+      if (sub == 0) {
+        nrm[c] = static_cast<float>(nn);
+        K[c] = id >= 0 ? pkey(static_cast<float>(dd), id) : ~0ull;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. sort (key, slot) ascending over the first P keys, the least power of
+  // two >= the candidate count (every later key is the ~0 sentinel)
+  int P = 32;
+  while (P < nc) P <<= 1;
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (tid < P / 2) {
+        const int i = (tid / stride) * 2 * stride + (tid % stride), j = i + stride;
+        const bool asc = (i & size) == 0;
+        const unsigned long long a = K[i], b = K[j];
+        if ((a > b) == asc) {
+          K[i] = b;
+          K[j] = a;
+          const uint8_t t = slot[i];
+          slot[i] = slot[j];
+          slot[j] = t;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // deduplicate (equal keys are the same id) into prune order
+  if (warp == 0) {
+    int nu = 0;
+    for (int c0 = 0; c0 < kCandMax; c0 += 32) {
+      const int c = c0 + lane;
+      const unsigned long long k = K[c];
+      const bool keep = k != ~0ull && (c == 0 || K[c - 1] != k);
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) U[nu + __popc(m & ((1u << lane) - 1u))] = static_cast<uint8_t>(c);
+      nu += __popc(m);
+    }
+    if (lane == 0) misc[1] = nu;
+  }
+  for (int w = tid; w < kCandMax * 8; w += kTcPruneThreads) bits[w] = 0u;
+  __syncthreads();
+  const int V = misc[1];
+
+  if (append_if_fits && V <= R) {
+    // every unique candidate fits: it becomes the row
+    if (warp == 0) {
+      for (int u = lane; u < V; u += 32) row[u] = static_cast<int32_t>(K[U[u]] & 0xffffffffu);
+      for (int j = V + lane; j < adj_stride; j += 32) row[j] = -1;
+    }
+    return;
+  }
+
+  // 3. the pruning relation of every pair i < j, as bits
+  const uint32_t xs = static_cast<uint32_t>(__cvta_generic_to_shared(X));
+  const int nti = (V + 15) >> 4, ntj = (V + 7) >> 3;
+  const int g = lane >> 2, cq = lane & 3;
+  for (int ti = warp; ti < nti; ti += kTcPruneThreads / 32) {
+    // A fragments of rows ti*16 .. +15, every k step (16 coordinates)
+    uint32_t af[8][4];
+    {
+      const int r = (lane & 7) + ((lane >> 3) & 1) * 8, kofs = (lane >> 4) * 8;
+      const int i = ti * 16 + r;
+      const int srow = i < V ? slot[U[i]] : kCandMax;
+      const uint32_t rowaddr = xs + static_cast<uint32_t>((srow * kTcPruneStride + kofs) * 2);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        if (kk < segs) ldsm_x4(rowaddr + kk * 32, af[kk][0], af[kk][1], af[kk][2], af[kk][3]);
+    }
+    // this thread's two rows of the accumulator: g and g + 8
+    const int i0 = ti * 16 + g, i1 = i0 + 8;
+    const float n0 = i0 < V ? nrm[slot[U[i0]]] : 0.f, n1 = i1 < V ? nrm[slot[U[i1]]] : 0.f;
+    for (int tj = (ti * 16) >> 3; tj < ntj; ++tj) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      {
+        const int n = lane & 7, kofs = ((lane >> 3) & 1) * 8 + (lane >> 4) * 16;
+        const int j = tj * 8 + n;
+        const int srow = j < V ? slot[U[j]] : kCandMax;
+        const uint32_t rowaddr = xs + static_cast<uint32_t>((srow * kTcPruneStride) * 2);
+#pragma unroll
+        for (int kk = 0; kk < 8; kk += 2) {
+          if (kk + 1 < segs) {
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4(rowaddr + static_cast<uint32_t>((kk * 16 + kofs) * 2), b0, b1, b2, b3);
+            mma_bf16_16816(acc, af[kk], b0, b1);
+            mma_bf16_16816(acc, af[kk + 1], b2, b3);
+          } else if (kk < segs) {
+            uint32_t b0, b1;
+            ldsm_x2(rowaddr + static_cast<uint32_t>((kk * 16 + (kofs & 8)) * 2), b0, b1);
+            mma_bf16_16816(acc, af[kk], b0, b1);
+          }
+        }
+      }
+      // accumulator (row g / g+8, columns 2cq, 2cq+1) -> pruning bits
+      unsigned byte0 = 0u, byte1 = 0u;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = tj * 8 + 2 * cq + e;
+        if (j < V) {
+          const int sj = slot[U[j]];
+          const float nj = nrm[sj];
+          const float dpj = __uint_as_float(static_cast<unsigned>(K[U[j]] >> 32));
+          // |c_i|^2 + |c_j|^2 and 2 c_i.c_j are exact integers below 2^24, so
+          // is their difference: the same float row_dist gives
+          const float d0 = (n0 + nj) - 2.f * acc[e];
+          const float d1 = (n1 + nj) - 2.f * acc[2 + e];
+          if (i0 < j && alpha * d0 <= dpj) byte0 |= 1u << (2 * cq + e);
+          if (i1 < j && alpha * d1 <= dpj) byte1 |= 1u << (2 * cq + e);
+        }
+      }
+      byte0 |= __shfl_xor_sync(kFull, byte0, 1);
+      byte0 |= __shfl_xor_sync(kFull, byte0, 2);
+      byte1 |= __shfl_xor_sync(kFull, byte1, 1);
+      byte1 |= __shfl_xor_sync(kFull, byte1, 2);
+      if (cq == 0) {
+        uint8_t* bb = reinterpret_cast<uint8_t*>(bits);
+        if (i0 < V) bb[i0 * 32 + tj] = static_cast<uint8_t>(byte0);
+        if (i1 < V) bb[i1 * 32 + tj] = static_cast<uint8_t>(byte1);
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. keep candidates in order; each kept one prunes the later ones of its row
+  if (warp == 0) {
+    unsigned gone = 0u;  // lane w < 8: candidates 32w .. 32w + 31
+    int kept = 0;
+    for (int i = 0; i < V && kept < R; ++i) {
+      const unsigned gw = __shfl_sync(kFull, gone, i >> 5);
+      if ((gw >> (i & 31)) & 1u) continue;
+      if (lane == 0) row[kept] = static_cast<int32_t>(K[U[i]] & 0xffffffffu);
+      ++kept;
+      if (lane < 8) gone |= bits[i * 8 + lane];
+    }
+    for (int j = kept + lane; j < adj_stride; j += 32) row[j] = -1;
+  }
 }
 
 // (j << 32 | p) for every new edge p -> j of the batch; ~0 for empty slots.
@@ -277,11 +562,17 @@ cudaError_t dmalloc(T** p, size_t n) {
 
 using namespace ann;
 
-extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
-                                   float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
-                                   int32_t* entry_out) {
+extern "C" int ann_build_graph_gpu_ex(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                                      float alpha, int32_t L_build, uint64_t seed, int32_t engine,
+                                      int32_t* adj_out, int32_t* entry_out) {
   if (!base || !adj_out) return set_error(ANN_EINVAL, "ann_build_graph_gpu: NULL buffer");
   if (dtype != ANN_U8 && dtype != ANN_F32) return set_error(ANN_EINVAL, "ann_build_graph_gpu: unknown dtype");
+  if (engine < ANN_BUILD_AUTO || engine > ANN_BUILD_CUDA_CORES)
+    return set_error(ANN_EINVAL, "ann_build_graph_gpu: unknown engine %d", engine);
+  const bool tc_ok = dtype == ANN_U8 && d <= 128;
+  if (engine == ANN_BUILD_TENSOR_CORES && !tc_ok)
+    return set_error(ANN_EINVAL, "ann_build_graph_gpu: the tensor-core prune needs uint8 data with d <= 128 (d=%d)", d);
+  const bool use_tc = tc_ok && engine != ANN_BUILD_CUDA_CORES;
   if (n < 2 || n >= INT32_MAX || R < 1 || R > kMaxR || L_build < R || L_build > kCandMax - R ||
       d < 16 || d % 16 || d > kMaxD || !(alpha >= 1.0f))
     return set_error(ANN_EINVAL,
@@ -424,6 +715,9 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
                                     starts, nsel, (int)pmax), "cub sizing");
   GB_TRY(dmalloc(reinterpret_cast<uint8_t**>(&cub_tmp), std::max(cub_bytes, sel_bytes)), "cudaMalloc sort scratch");
   cudaStream_t st = 0;
+  if (use_tc)
+    GB_TRY(cudaFuncSetAttribute(prune_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kTcPruneSmem)), "prune shared memory");
 
   SearchArgs a{};
   a.n = (int32_t)n;
@@ -464,7 +758,10 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
       GB_TRY(launch_search(a, pb, st), "build search");
       // forward prune: pool = the search results, plus the current row
       fill_pool_meta<<<(b + 255) / 256, 256, 0, st>>>(b, pool, off, cnt);
-      if (dtype == ANN_U8)
+      if (use_tc)
+        prune_tc_kernel<<<b, kTcPruneThreads, kTcPruneSmem, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, 1, 0,
+                                                                  adj_d, stride);
+      else if (dtype == ANN_U8)
         prune_kernel<true><<<(b + 3) / 4, 128, 0, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, b, 1, 0, adj_d, stride);
       else
         prune_kernel<false><<<(b + 3) / 4, 128, 0, st>>>(base_d, d, R, al, nodes, cand_ids, off, cnt, b, 1, 0, adj_d, stride);
@@ -485,6 +782,9 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
       const int32_t g = meta[0], m_valid = meta[1];
       if (g > 0) {
         group_tasks<<<(g + 255) / 256, 256, 0, st>>>(starts, g, m_valid, target, task_node, off, cnt);
+        // back edges: mostly a few sources appended to a row that has room, so
+        // the warp-per-node kernel (whose fixed cost per task is lower)
+        // serves them with either engine
         if (dtype == ANN_U8)
           prune_kernel<true><<<(g + 3) / 4, 128, 0, st>>>(base_d, d, R, al, task_node, src, off, cnt, g, 1, 1, adj_d, stride);
         else
@@ -502,4 +802,10 @@ extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, i
   cleanup();
 #undef GB_TRY
   return ANN_OK;
+}
+
+extern "C" int ann_build_graph_gpu(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                                   float alpha, int32_t L_build, uint64_t seed, int32_t* adj_out,
+                                   int32_t* entry_out) {
+  return ann_build_graph_gpu_ex(base, dtype, n, d, R, alpha, L_build, seed, ANN_BUILD_AUTO, adj_out, entry_out);
 }

@@ -95,3 +95,32 @@ def test_gpu_pq_encoder_equals_host_encoder():
     cb, codes = ann.build_pq(base, 32, n_train=5000, iters=4, kpp_uniforms=u)
     cb2, codes2 = ann.build_pq(base, 32, n_train=5000, iters=4, kpp_uniforms=u, encode_device="gpu")
     assert np.array_equal(cb, cb2) and np.array_equal(codes, codes2)
+
+
+@pytest.mark.parametrize("n,d,R,L_build", [(30_000, 128, 64, 128), (12_000, 128, 96, 128),
+                                           (8_000, 64, 32, 96), (6_000, 48, 24, 64)])
+def test_gpu_build_tensor_prune_equals_cuda_cores(n, d, R, L_build):
+    """RobustPrune with the candidate distances from BF16 MMAs (exact for
+    uint8) makes the same decisions as the CUDA-core prune: the graphs are
+    identical, row for row.  d = 48 has an odd number of 16-coordinate MMA
+    steps; R = 96 fills candidate sets up to 256."""
+    if d == 128:
+        base = datagen.sift_like().base(n)
+    else:
+        base = np.random.default_rng(d).integers(0, 256, size=(n, d)).astype(np.uint8)
+    t_adj, t_entry = ann.build_graph(base, R, 1.2, L_build, seed=11, device="gpu", engine="tensor")
+    c_adj, c_entry = ann.build_graph(base, R, 1.2, L_build, seed=11, device="gpu", engine="cuda")
+    assert t_entry == c_entry
+    assert np.array_equal(t_adj, c_adj)
+    _check_rows(t_adj, R)
+
+
+def test_gpu_build_tensor_engine_needs_small_uint8():
+    x = np.zeros((100, 16), np.float32)
+    with pytest.raises(ann.AnnError) as e:
+        ann.build_graph(x, 8, 1.2, 16, device="gpu", engine="tensor")
+    assert e.value.status == ann._abi.ANN_EINVAL
+    y = np.zeros((100, 144), np.uint8)
+    with pytest.raises(ann.AnnError) as e:
+        ann.build_graph(y, 8, 1.2, 16, device="gpu", engine="tensor")
+    assert e.value.status == ann._abi.ANN_EINVAL
