@@ -390,6 +390,9 @@ def run_ours(args, rank: int, world: int):
                                       int(NCU_BYTES_PER_EXPANSION[kernel_name][1] * st.expansions / args.steps)),
                      "peak_source": f"measured in-run: random {fetch_bytes} B reads of host pinned memory (the search's per-expansion fetch) by a full-occupancy probe kernel (ann_probe_read_bandwidth)",
                      "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                     "achieved_what": f"algorithmic bytes ({fetch_bytes} B per expansion: vector + neighbour ids) x expansions / the launch's CUDA-event time",
+                     "frac_of_nominal_pcie": round(achieved / 64.0, 4),
+                     "nominal_pcie_gbs": 64.0,
                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6400.0),
                      "hbm_peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in measured_peaks() else "fallback (6.4 TB/s, one earlier B300 measurement)"},
         "setup_s": round(setup_s, 1),
