@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 // reads it once per tile (a tile ahead), so a CTA's first tiles no longer
 // admit a stream of candidates that another CTA has already ruled out.
 // Each warpgroup writes its lists as one part; a fold kernel merges the parts
-// with the running top-k after each chunk of the base.
+// with the running top-k after each chunk of the base.  The first chunk is
+// small, so that the running top-k bounds every later chunk from its start.
 // Every wait on an mbarrier is bounded: past ~2 s the CTA sets an abort flag,
 // every role leaves its loop, the producer waits (bounded) for the copies it
 // issued, tensor memory is freed, and the host sees the error word.
@@ -784,8 +785,13 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && !bf16_row_map(&qmap, qb, q_rows, dp)) e = cudaErrorInvalidValue;
-  for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
-    const int64_t cn = (n - c0 < chunk) ? n - c0 : chunk;
+  // The first chunk is small (2^17 rows): once it is folded, every query's
+  // running k-th best over it bounds the keys of all later chunks, so their
+  // CTAs start with a tight bound instead of each warming up its own.
+  const int64_t seed_rows = chunk < (1ll << 17) ? chunk : (1ll << 17);
+  for (int64_t c0 = 0; c0 < n && e == cudaSuccess;) {
+    const int64_t cmax = c0 == 0 ? seed_rows : chunk;
+    const int64_t cn = (n - c0 < cmax) ? n - c0 : cmax;
     const int64_t map_rows = (cn + kTcN - 1) / kTcN * kTcN;
     to_bf16_rows<<<static_cast<unsigned>((map_rows * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn,
                                                                                        map_rows, d, dp, xb, xn);
@@ -810,6 +816,7 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
                     stream>>>(qmap, xmap, ta);
     topk_fold<<<static_cast<unsigned>(nq), 256, 0, stream>>>(keys, nslots, k);
     e = cudaGetLastError();
+    c0 += cn;
   }
   if (e == cudaSuccess) {
     topk_write<<<static_cast<unsigned>((nq * k + 255) / 256), 256, 0, stream>>>(keys, nq, nslots, k, ids, dists);

@@ -90,3 +90,14 @@ def test_tensor_engine_rejects_float_data():
     with pytest.raises(ann.AnnError) as e:
         ann.knn_exact(x, x[:2], 3, engine="tensor")
     assert e.value.status == ann._abi.ANN_EINVAL
+
+
+@pytest.mark.parametrize("n", [131_072, 131_077])
+def test_tensor_knn_seed_chunk_boundary(n):
+    """The base is processed as a first chunk of 2^17 rows, then chunks of
+    2^22: exactly the first chunk, and the first chunk plus a 5-row second
+    chunk (one ragged tile), bit-exact against the oracle."""
+    mx = datagen.sift_like()
+    base, q = mx.base(n), mx.queries(70)
+    ids, d = ann.knn_exact(base, q, 12, engine="tensor")
+    _exact(ids, d, *oracle.knn(base, q, 12))
