@@ -215,6 +215,28 @@ int ann_search_dev_kernel_grained(ann_index* index, const void* queries, int64_t
                                   int32_t L, int32_t depth, int32_t* ids, float* dists,
                                   const ann_trace* trace, void* stream);
 
+/*
+ * CPU-agent I/O: the paper's I/O stack as it describes it (Section
+ * "Resource-Efficient Query-Grained Concurrent I/O Stack": each warp writes
+ * its block address into a request array in mapped pinned host memory, a CPU
+ * agent serves the requests, and the warp checks a completion signal before
+ * it uses the data), as an ablation against the warps reading node blocks
+ * themselves (ann_search).  Same arguments and results as ann_search (host
+ * buffers, k, L, depth; identical ids, distances and expansion counts), for a
+ * PQ index with its node blocks in host pinned memory.
+ *  agent_threads: host threads serving the requests (0..64); each owns a
+ *    fixed share of the warps' request entries and copies a requested block
+ *    into that entry's staging slot (mapped pinned memory), then writes the
+ *    entry's completion word.  The warp then reads the block from the slot.
+ *  wait_us: bound on one wait for a completion (1 .. 6e7); past it the query
+ *    stops, the call returns ANN_ETIMEOUT, and the index stays usable.
+ *  seconds (may be NULL): host wall time from the launch to the kernel's end.
+ * Blocking; one warp per query whatever ann_set_warps_per_query set.
+ */
+int ann_search_cpu_agent(ann_index* index, const void* queries, int64_t nq, int32_t k, int32_t L,
+                         int32_t depth, int32_t agent_threads, int64_t wait_us, int32_t* ids,
+                         float* dists, ann_search_stats* stats, double* seconds);
+
 /* Wait for `stream`, then report (and reset) the totals and failures of the
  * ann_search_dev calls since the previous ann_sync. */
 int ann_sync(ann_index* index, void* stream, ann_search_stats* stats);

@@ -164,6 +164,23 @@ class Index:
                                      ctypes.c_void_p(dists.data_ptr()),
                                      ctypes.byref(tr) if tr else None, st))
 
+    def search_cpu_agent(self, queries, k: int, L: int, depth: int = 1, agent_threads: int = 4,
+                         wait_us: int = 2_000_000, check: bool = True):
+        """Host-buffer search with CPU-agent I/O (the ablation of the paper's
+        mapped request array; see ann_search_cpu_agent).  Returns (ids, dists,
+        stats, seconds); with check=False an ANN_ETIMEOUT does not raise."""
+        q = _c(queries, self._np_dtype())
+        nq = q.shape[0] if q.ndim == 2 else 0
+        ids = np.empty((nq, k), np.int32)
+        dists = np.empty((nq, k), np.float32)
+        stats = SearchStats()
+        secs = ctypes.c_double(0.0)
+        rc = _lib().ann_search_cpu_agent(self._h, _p(q), nq, k, L, depth, agent_threads, wait_us,
+                                         _p(ids), _p(dists), ctypes.byref(stats), ctypes.byref(secs))
+        if check or rc != _abi.ANN_ETIMEOUT:
+            _check(rc)
+        return ids, dists, stats, secs.value
+
     def search_dev_kernel_grained(self, queries, k: int, L: int, depth: int, ids, dists,
                                   stream=None, trace: dict | None = None):
         """search_dev with kernel-grained I/O (the ablation: a grid-wide

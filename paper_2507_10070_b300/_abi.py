@@ -23,7 +23,7 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_load_graph_file", "ann_free", "ann_index_block_bytes", "ann_index_size",
            "ann_set_warps_per_query",
            "ann_search", "ann_search_dev", "ann_sync", "ann_search_dev_noalloc",
-           "ann_search_dev_kernel_grained",
+           "ann_search_dev_kernel_grained", "ann_search_cpu_agent",
            "ann_build_pq", "ann_build_graph",
            "ann_knn_exact", "ann_knn_exact_ex", "ann_probe_read_bandwidth", "ann_serve_create", "ann_serve_submit",
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
@@ -119,6 +119,9 @@ def lib():
                                  ctypes.POINTER(SearchStats)]
         L.ann_search_dev.restype = ctypes.c_int
         L.ann_search_dev.argtypes = [P, P, I64, I32, I32, I32, P, P, ctypes.POINTER(Trace), P]
+        L.ann_search_cpu_agent.restype = ctypes.c_int
+        L.ann_search_cpu_agent.argtypes = [P, P, I64, I32, I32, I32, I32, I64, P, P,
+                                           ctypes.POINTER(SearchStats), ctypes.POINTER(ctypes.c_double)]
         L.ann_search_dev_kernel_grained.restype = ctypes.c_int
         L.ann_search_dev_kernel_grained.argtypes = [P, P, I64, I32, I32, I32, P, P,
                                                     ctypes.POINTER(Trace), P]

@@ -35,6 +35,13 @@ constexpr int kMaxD = 512;
 constexpr int kMaxM = 64;
 constexpr int kVisLog = 8192;  // entries of a query's visited-set clear log
 
+// One CPU-agent request: the node whose block a warp wants, and a sequence
+// number (written last) that tells the host the entry is new.
+struct AgentReq {
+  int32_t node;
+  uint32_t seq;
+};
+
 // Everything one launch of the search kernel reads or writes.
 struct SearchArgs {
   // index
@@ -54,6 +61,16 @@ struct SearchArgs {
   int32_t adj_stride;       // ids per adjacency row (multiple of 4)
   const int32_t* id_map;    // caller's id of each stored node, written to the results (HBM), or null
   unsigned* grid_bar;       // kernel-grained I/O ablation: grid barrier state (4 words), or null
+  // CPU-agent I/O (the paper's mapped request array, an ablation); agent_req
+  // null = the warps read node blocks themselves.  Per resident warp, D + 1
+  // entries: the warp writes a request (node, sequence number) into
+  // agent_req, a host thread copies the block into that entry's staging slot
+  // and then writes the sequence number into agent_done.
+  AgentReq* agent_req;      // [warps * (D + 1)], host-mapped, written by the GPU
+  const unsigned* agent_done;      // [warps * (D + 1)], host-mapped, written by the host
+  const uint8_t* agent_stage;      // [warps * (D + 1) * slot_bytes], host-mapped, written by the host
+  unsigned* agent_seq;      // [warps * (D + 1)] last sequence number issued (device memory)
+  int64_t agent_wait_ns;    // bound on one wait for a completion
   // batch
   const void* queries;
   int32_t nq, k, L, depth;

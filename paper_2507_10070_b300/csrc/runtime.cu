@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -381,9 +382,18 @@ int validate_search(const ann_index* ix, const void* q, int64_t nq, int k, int L
 // Enqueue one search of nq device-resident queries on `st`.
 bool rerank_mode(int mode) { return mode == kModeBF16 || mode == kModeFP8 || mode == kModePqF32; }
 
+// Device-visible buffers of the CPU-agent I/O ablation (see SearchArgs).
+struct AgentBufs {
+  AgentReq* req;
+  const unsigned* done;
+  const uint8_t* stage;
+  unsigned* seq;
+  int64_t wait_ns;
+};
+
 int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int depth, int32_t* ids,
                    float* dists, const ann_trace* tr, cudaStream_t st, bool timed,
-                   bool kernel_grained = false) {
+                   bool kernel_grained = false, const AgentBufs* agent = nullptr) {
   if (nq == 0) return ANN_OK;
   const int slot_bytes = ix->slot_bytes;
   // precision variants: keep the top rerank_mult*k expanded by navigation
@@ -402,7 +412,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
   }
   SearchPlan plan;
   cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, slot_bytes, depth, L, k, nq, &plan, ix->n,
-                              kernel_grained ? 1 : ix->wpq);
+                              (kernel_grained || agent) ? 1 : ix->wpq);
   if (e != cudaSuccess) return cuda_error(e, "plan search");
   const size_t want = (size_t)plan.tables * (size_t)plan.vis_words;
   if (want > ix->vis_words) {
@@ -425,7 +435,7 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
     e = ix->vis_log.ensure(log_bytes);
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc visited log");
   }
-  SearchArgs a;
+  SearchArgs a{};
   a.n = (int32_t)ix->n;
   a.d = ix->d;
   a.R = ix->R;
@@ -460,6 +470,13 @@ int enqueue_search(ann_index* ix, const void* q, int64_t nq, int k, int L, int d
     e = cudaMemcpyAsync(ix->grid_bar.p, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_error(e, "grid barrier state");
     a.grid_bar = static_cast<unsigned*>(ix->grid_bar.p);
+  }
+  if (agent) {
+    a.agent_req = agent->req;
+    a.agent_done = agent->done;
+    a.agent_stage = agent->stage;
+    a.agent_seq = agent->seq;
+    a.agent_wait_ns = agent->wait_ns;
   }
   a.queries = q;
   a.nq = (int32_t)nq;
@@ -610,6 +627,126 @@ int ann_search_dev_kernel_grained(ann_index* ix, const void* queries, int64_t nq
   rc = enqueue_search(ix, queries, nq, k, L, depth, ids, dists, trace,
                       static_cast<cudaStream_t>(stream), false, true);
   if (rc == ANN_OK) ix->pending_queries += nq;
+  return rc;
+}
+
+// One host agent thread: serve the request entries [lo, hi) until *stop.
+// A new sequence number in an entry is a request: copy the node's block
+// into the entry's staging slot, then publish the number in `done` (release
+// order: the GPU that reads the number reads the bytes after it).
+void agent_serve(AgentReq* req, unsigned* done, uint8_t* stage, const uint8_t* blocks, int block_bytes,
+                 int slot_bytes, int64_t n, size_t lo, size_t hi, const std::atomic<bool>* stop) {
+  std::vector<unsigned> last(hi - lo, 0u);
+  while (!stop->load(std::memory_order_acquire)) {
+    bool any = false;
+    for (size_t e = lo; e < hi; ++e) {
+      const unsigned sq = __atomic_load_n(&req[e].seq, __ATOMIC_ACQUIRE);
+      if (sq == last[e - lo]) continue;
+      const int32_t node = __atomic_load_n(&req[e].node, __ATOMIC_RELAXED);
+      if (node >= 0 && node < n)
+        std::memcpy(stage + e * slot_bytes, blocks + static_cast<size_t>(node) * block_bytes, slot_bytes);
+      __atomic_store_n(&done[e], sq, __ATOMIC_RELEASE);
+      last[e - lo] = sq;
+      any = true;
+    }
+    if (!any) std::this_thread::yield();
+  }
+}
+
+int ann_search_cpu_agent(ann_index* ix, const void* queries, int64_t nq, int32_t k, int32_t L, int32_t depth,
+                         int32_t agent_threads, int64_t wait_us, int32_t* ids, float* dists,
+                         ann_search_stats* stats, double* seconds) {
+  int rc = validate_search(ix, queries, nq, k, L, depth, ids, dists);
+  if (rc != ANN_OK) return rc;
+  if (ix->mode != kModePqU8 || ix->blocks_in_hbm || !ix->blocks_host)
+    return set_error(ANN_EINVAL, "cpu agent: needs a PQ index with its node blocks in host pinned memory");
+  if (agent_threads < 0 || agent_threads > 64 || wait_us < 1 || wait_us > 60000000)
+    return set_error(ANN_EINVAL, "cpu agent: need 0 <= agent_threads <= 64 and 1 <= wait_us <= 6e7");
+  BusyGuard guard(ix);
+  if (!guard.ok) return set_error(ANN_EBUSY, "index is busy with another search");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (seconds) *seconds = 0.0;
+  if (nq == 0) return ANN_OK;
+  cudaStream_t st = ix->stream;
+  SearchPlan plan;
+  cudaError_t e = plan_search(ix->mode, ix->R, ix->M, ix->d, ix->slot_bytes, depth, L, k, nq, &plan, ix->n, 1);
+  if (e != cudaSuccess) return cuda_error(e, "plan search");
+  const size_t entries = static_cast<size_t>(plan.blocks) * plan.warps_per_block * (depth + 1);
+  AgentReq* req = nullptr;
+  unsigned* done = nullptr;
+  uint8_t* stage = nullptr;
+  unsigned* seq = nullptr;
+  auto free_all = [&] {
+    if (req) cudaFreeHost(req);
+    if (done) cudaFreeHost(done);
+    if (stage) cudaFreeHost(stage);
+    cudaFree(seq);
+  };
+  e = cudaHostAlloc(reinterpret_cast<void**>(&req), entries * sizeof(AgentReq), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&done), entries * 4, cudaHostAllocMapped);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&stage), entries * ix->slot_bytes, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaMalloc(&seq, entries * 4);
+  if (e == cudaSuccess) e = cudaMemset(seq, 0, entries * 4);
+  const size_t qbytes = (size_t)nq * ix->d;
+  if (e == cudaSuccess) e = ix->q_stage.ensure(qbytes);
+  if (e == cudaSuccess) e = ix->ids_stage.ensure((size_t)nq * k * 4);
+  if (e == cudaSuccess) e = ix->dists_stage.ensure((size_t)nq * k * 4);
+  if (e != cudaSuccess) {
+    free_all();
+    return cuda_error(e, "cpu agent buffers");
+  }
+  std::memset(req, 0, entries * sizeof(AgentReq));
+  std::memset(done, 0, entries * 4);
+  AgentBufs ab;
+  void* dp = nullptr;
+  e = cudaHostGetDevicePointer(&dp, req, 0);
+  ab.req = static_cast<AgentReq*>(dp);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, done, 0);
+  ab.done = static_cast<const unsigned*>(dp);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, stage, 0);
+  ab.stage = static_cast<const uint8_t*>(dp);
+  ab.seq = seq;
+  ab.wait_ns = wait_us * 1000;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ix->q_stage.p, queries, qbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_all();
+    return cuda_error(e, "cpu agent set-up");
+  }
+  std::atomic<bool> stop{false};
+  std::vector<std::thread> agents;
+  for (int t = 0; t < agent_threads; ++t)
+    agents.emplace_back(agent_serve, req, done, stage, ix->blocks_host, ix->block_bytes, ix->slot_bytes, ix->n,
+                        entries * t / agent_threads, entries * (t + 1) / agent_threads, &stop);
+  int32_t* ids_d = static_cast<int32_t*>(ix->ids_stage.p);
+  float* dists_d = static_cast<float*>(ix->dists_stage.p);
+  const auto t0 = std::chrono::steady_clock::now();
+  rc = enqueue_search(ix, ix->q_stage.p, nq, k, L, depth, ids_d, dists_d, nullptr, st, true, false, &ab);
+  if (rc == ANN_OK) {
+    e = cudaStreamSynchronize(st);  // the agents serve requests until the kernel is done
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  stop.store(true, std::memory_order_release);
+  for (auto& t : agents) t.join();
+  if (rc == ANN_OK && e != cudaSuccess) rc = cuda_error(e, "cpu agent search");
+  if (rc == ANN_OK) {
+    e = cudaMemcpyAsync(ids, ids_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dists, dists_d, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_error(e, "copy results");
+  }
+  if (rc == ANN_OK) {
+    ann_search_stats local{};
+    ann_search_stats* sp = stats ? stats : &local;
+    rc = collect(ix, st, nq, sp, true);
+    // the one way a query stops early here: a wait for the agent ran out
+    if (rc == ANN_ENOMEM)
+      rc = set_error(ANN_ETIMEOUT, "cpu agent: a wait for the host agent ran out (%lld queries failed)",
+                     (long long)sp->n_failed);
+  } else {
+    cudaStreamSynchronize(st);
+  }
+  free_all();
   return rc;
 }
 

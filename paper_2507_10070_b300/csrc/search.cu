@@ -70,6 +70,26 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
   }
 }
 
+__device__ __forceinline__ unsigned ld_relaxed_sys_u32(const void* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_sys_u32(void* p, unsigned v) {
+  asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// 16 bytes of host-mapped memory, read afresh (not from a cached copy).
+__device__ __forceinline__ uint4 ld_cv_u4(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.cv.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
 __device__ __forceinline__ long long global_timer_ns() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -485,6 +505,35 @@ __device__ __forceinline__ unsigned navigation_dist(const SearchArgs& a, const u
   return exact_dist_warp<MODE>(a, qs, w, lane);
 }
 
+// CPU-agent I/O: post the request of entry e (lane 0).  The node goes first,
+// the new sequence number last, with a system-scope fence between them, so
+// a host thread that sees the number also sees the node.
+__device__ __forceinline__ void agent_post(const SearchArgs& a, size_t e, unsigned node) {
+  const unsigned sq = a.agent_seq[e] + 1u;
+  a.agent_seq[e] = sq;
+  st_relaxed_sys_u32(&a.agent_req[e].node, node);
+  __threadfence_system();
+  st_relaxed_sys_u32(&a.agent_req[e].seq, sq);
+}
+
+// Wait (lane 0) until the host has served entry e's latest request, at most
+// a.agent_wait_ns; false if the wait ran out.  The completion word is read
+// over PCIe, so the polls back off.
+__device__ bool agent_wait(const SearchArgs& a, size_t e) {
+  const unsigned want = a.agent_seq[e];
+  const long long t0 = global_timer_ns();
+  unsigned ns = 32;
+  for (;;) {
+    if (ld_relaxed_sys_u32(a.agent_done + e) == want) {
+      __threadfence_system();  // the staging slot's bytes are read after this
+      return true;
+    }
+    if (global_timer_ns() - t0 > a.agent_wait_ns) return false;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+}
+
 template <int MODE, int NB, bool PF = false>
 __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned char* ws,
                           const WarpSmem& lay, uint32_t* vis, uint32_t* vlog, int lane) {
@@ -629,7 +678,10 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
   // node's, which have returned), and the list merge of its candidates still
   // happens in its own step, so the search is unchanged.  A separate
   // instance (PF), so that depths 0 and 1 keep the leaner kernel.
-  const bool prefetch = PF && MODE == kModePqU8 && D >= 2 && !a.grid_bar;
+  const bool prefetch = PF && MODE == kModePqU8 && D >= 2 && !a.grid_bar && !a.agent_req;
+  // CPU-agent I/O: this warp's D + 1 request entries
+  const size_t agent_base =
+      (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * static_cast<size_t>(D + 1);
   bool pre = false;  // the node at the FIFO head has its loads in flight
   int pw[NB];
   unsigned pword[NB], pold[NB];
@@ -713,19 +765,37 @@ __device__ void run_query(const SearchArgs& a, const QueryJob& job, unsigned cha
         if (sel == 0) s.flags[ia] = 1; else pend.flags[ib] = 1;
         ring_key[slot] = key;
       }
-      const uint8_t* src = (MODE == kModePqU8)
-                               ? a.blocks + static_cast<size_t>(v) * a.block_bytes
-                               : reinterpret_cast<const uint8_t*>(
-                                     a.adj + static_cast<size_t>(v) * a.adj_stride);
-      unsigned char* dst = ring + slot * slot_bytes;
-      for (int off = lane * 16; off < slot_bytes; off += 512) cp_async_16(dst + off, src + off);
-      cp_async_commit();
+      if (MODE == kModePqU8 && a.agent_req) {
+        // the host agent copies the block into this entry's staging slot
+        if (lane == 0) agent_post(a, agent_base + slot, v);
+      } else {
+        const uint8_t* src = (MODE == kModePqU8)
+                                 ? a.blocks + static_cast<size_t>(v) * a.block_bytes
+                                 : reinterpret_cast<const uint8_t*>(
+                                       a.adj + static_cast<size_t>(v) * a.adj_stride);
+        unsigned char* dst = ring + slot * slot_bytes;
+        for (int off = lane * 16; off < slot_bytes; off += 512) cp_async_16(dst + off, src + off);
+        cp_async_commit();
+      }
       ++inflight;
       __syncwarp();  // lane 0's flag and ring_key writes are seen by every lane
     }
     if (inflight > D || (sel < 0 && inflight > 0)) {
       // ---- a5: wait for this warp's oldest fetch only
-      cp_async_wait_pending(inflight - 1);
+      if (MODE == kModePqU8 && a.agent_req) {
+        int ok = 1;
+        if (lane == 0) ok = agent_wait(a, agent_base + head) ? 1 : 0;
+        if (!__shfl_sync(kFull, ok, 0)) {
+          status = ANN_ETIMEOUT;
+          break;
+        }
+        const uint8_t* stg = a.agent_stage + (agent_base + head) * static_cast<size_t>(slot_bytes);
+        unsigned char* dst = ring + head * slot_bytes;
+        for (int off = lane * 16; off < slot_bytes; off += 512)
+          *reinterpret_cast<uint4*>(dst + off) = ld_cv_u4(stg + off);
+      } else {
+        cp_async_wait_pending(inflight - 1);
+      }
       __syncwarp();
       if (a.grid_bar) {  // kernel-grained ablation: the round's fetches all land first
         int all_done;
@@ -1425,12 +1495,6 @@ __global__ void __launch_bounds__(32 * W) search_kernel_wg(SearchArgs a, int sme
   }
 }
 
-__device__ __forceinline__ unsigned ld_relaxed_sys_u32(const void* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Persistent serving kernel: every warp claims published work items one at a
 // time (atomicCAS on the device head, against the published tail), runs the
 // search for it and writes the results straight into mapped host memory,
@@ -1698,7 +1762,7 @@ cudaError_t plan_search(int mode, int R, int M, int d, int slot_bytes, int depth
 
 cudaError_t launch_search(const SearchArgs& a, const SearchPlan& plan, cudaStream_t stream) {
   if (plan.wpq > 1) return launch_wg_table(plan.nb, plan.wpq)(a, plan, stream);
-  if (plan.pf && !a.grid_bar) return launch_pf_table(plan.nb)(a, plan, stream);
+  if (plan.pf && !a.grid_bar && !a.agent_req) return launch_pf_table(plan.nb)(a, plan, stream);
   return launch_table(plan.mode, plan.nb)(a, plan, stream);
 }
 

@@ -70,7 +70,7 @@ extern "C" int ann_search_dev_noalloc(ann_index* ix, const void* queries, int64_
   if (depth < 0 || depth > kMaxDepth) return set_error(ANN_EINVAL, "depth=%d out of range", depth);
   if (nq > 0 && (!queries || !ids || !dists)) return set_error(ANN_EINVAL, "queries, ids and dists are required");
   if (reinterpret_cast<uintptr_t>(queries) % 16) return set_error(ANN_EINVAL, "queries must be 16-byte aligned");
-  SearchArgs a;
+  SearchArgs a{};
   int mode = 0, slot_bytes = 0;
   int rc = index_search_view(ix, &a, &mode, &slot_bytes);
   if (rc != ANN_OK) return rc;
