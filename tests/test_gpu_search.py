@@ -44,12 +44,13 @@ def test_pq_search_bit_exact(u8_pq, pq_index, L, depth):
     assert stats.expansions == int(osteps.sum())
 
 
-@pytest.mark.parametrize("L", [2048, 4096])
+@pytest.mark.parametrize("L", [2048, 4096, 5120, 8192])
 @pytest.mark.parametrize("depth", [0, 1, 2, 4])
 def test_pq_search_long_lists_bit_exact(u8_pq, pq_index, L, depth):
     """From L = 2048 on, each step's candidates go to a short sorted pending
     buffer merged into the list only when full; selection and the entry bound
-    work on the union.  The list, and so every step, must stay the oracle's."""
+    work on the union.  The list, and so every step, must stay the oracle's
+    (up to L = 8192, the longest list the benchmarks use)."""
     q = u8_pq["q"][:48]
     ids, dists, stats, tr = pq_index.search(q, 10, L, depth, trace=True)
     oi, od, osteps = _oracle_pq(u8_pq, 10, L, depth, q=q)
