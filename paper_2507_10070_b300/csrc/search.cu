@@ -1121,6 +1121,7 @@ struct WgCtl {
   int act;                  // 1 = expand, 2 = stop
   int slot;                 // ring slot holding its block
   int len;                  // list length before this step's merge
+  int plen;                 // pending-buffer length before this step's merge
   int vis_count;            // visited-log entries of the query so far
   int cand_count;           // candidates entering the list this step
   int qi;                   // query the block works on
@@ -1200,6 +1201,13 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
 
   // ---- a2: entry node (warp 0)
   int len = 1, nres = 0, head = 0, inflight = 0, steps = 0, status = ANN_OK, first_open = 0;
+  // From L = kLazyL on, as in run_query: the step's candidates go to a sorted
+  // pending buffer (warp 0), merged into the list by all warps when full;
+  // the list is the first L entries of the union of both.
+  const bool lazy = L >= kLazyL;
+  unsigned long long* pkeys = reinterpret_cast<unsigned long long*>(ws + lay.pkeys);
+  unsigned char* pflags = ws + lay.pflags;
+  int plen = 0, pfirst_open = 0;
   const int max_steps = n + 1;
   if (warp == 0) {
     const uint8_t* code = a.codes + static_cast<size_t>(a.entry) * a.M;
@@ -1217,6 +1225,53 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     __syncwarp();
   }
 
+  // Merge sorted src[0..cs) (flags sf, or 0) into the list of length lv in
+  // place, all warps: rank them, move the list's tail right in rounds of W
+  // blocks (all reads of a round before its writes; entries only move right,
+  // so the rounds run top-down), then drop the new entries into their
+  // places; entries pushed past L fall off.  Returns the first changed
+  // position.  Ends with every thread synchronised.
+  auto wg_merge = [&](const unsigned long long* src, const unsigned char* sf, int cs, int lv) -> int {
+    for (int j = tid; j < cs; j += 32 * W) rank[j] = lower_bound_u64(keys, lv, src[j]);
+    __syncthreads();
+    const int pos0 = rank[0];
+    constexpr int kB = 256;  // entries per warp per round (8 per lane)
+    const int top_block = ((lv - 1) / kB) * kB;
+    const int low_block = (pos0 / kB) * kB;
+    for (int r0 = top_block; r0 >= low_block; r0 -= W * kB) {
+      const int b = r0 - warp * kB;
+      unsigned long long kv[8];
+      unsigned char fv[8];
+      int np[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = b + t * 32 + lane;
+        const bool live = b >= low_block && i >= pos0 && i < lv;
+        kv[t] = live ? keys[i] : 0ull;
+        fv[t] = live ? flags[i] : 0;
+        np[t] = !live ? L : (i >= rank[cs - 1] ? i + cs : i + upper_bound_i32(rank, cs, i));
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (np[t] < L) {
+          keys[np[t]] = kv[t];
+          flags[np[t]] = fv[t];
+        }
+      }
+      __syncthreads();
+    }
+    for (int j = tid; j < cs; j += 32 * W) {
+      const int p = j + rank[j];
+      if (p < L) {
+        keys[p] = src[j];
+        flags[p] = sf ? sf[j] : 0;
+      }
+    }
+    __syncthreads();
+    return pos0;
+  };
+
   for (;;) {
     // ---- a3-a5 (warp 0): select, issue fetches, and wait for the oldest
     // when more than D are in flight or nothing is selectable
@@ -1224,26 +1279,49 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       int act = 0, slot_u = 0;
       unsigned long long ukey = 0;
       do {
-        int sel = -1;
+        int sel = -1, src = 0;  // src 0: list entry sel, 1: pending entry sel
+        unsigned long long key = 0;
         if (status == ANN_OK) {
+          int ia = -1, ib = -1;
           for (int b = first_open; b < len; b += 32) {
             const int i = b + lane;
             const unsigned m = __ballot_sync(kFull, i < len && flags[i] == 0);
             if (m) {
-              sel = b + __ffs(m) - 1;
+              ia = b + __ffs(m) - 1;
               break;
             }
           }
-          first_open = sel >= 0 ? sel + 1 : len;
+          for (int b = pfirst_open; b < plen; b += 32) {
+            const int i = b + lane;
+            const unsigned m = __ballot_sync(kFull, i < plen && pflags[i] == 0);
+            if (m) {
+              ib = b + __ffs(m) - 1;
+              break;
+            }
+          }
+          first_open = ia >= 0 ? ia : len;
+          pfirst_open = ib >= 0 ? ib : plen;
+          // the smaller of the two, if its rank in the union is below L
+          if (ia >= 0 && (ib < 0 || keys[ia] < pkeys[ib])) {
+            key = keys[ia];
+            if (plen == 0 || ia + lower_bound_u64(pkeys, plen, key) < L) sel = ia;
+          } else if (ib >= 0) {
+            key = pkeys[ib];
+            if (ib + lower_bound_u64(keys, len, key) < L) {
+              sel = ib;
+              src = 1;
+            }
+          }
+          if (sel >= 0 && src == 0) first_open = sel + 1;
+          if (sel >= 0 && src == 1) pfirst_open = sel + 1;
         }
         if (sel >= 0) {
-          const unsigned long long key = keys[sel];
           const unsigned v = static_cast<unsigned>(key);
           int slot = head + inflight;
           if (slot > D) slot -= D + 1;
           __syncwarp();
           if (lane == 0) {
-            flags[sel] = 1;
+            if (src == 0) flags[sel] = 1; else pflags[sel] = 1;
             ring_key[slot] = key;
           }
           const uint8_t* src = a.blocks + static_cast<size_t>(v) * a.block_bytes;
@@ -1278,6 +1356,7 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
         ctl->slot = slot_u;
         ctl->ukey = ukey;
         ctl->len = len;
+        ctl->plen = plen;
         ctl->cand_count = 0;
       }
     }
@@ -1285,7 +1364,11 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     if (ctl->act == 2) break;
     const unsigned char* blk = ring + ctl->slot * slot_bytes;
     const int lenv = ctl->len;
-    const unsigned long long thr = (lenv == L) ? keys[L - 1] : kNoKey;
+    const int plenv = ctl->plen;
+    // a key at or above the L-th of list and pending buffer together cannot enter
+    const unsigned long long thr =
+        plenv == 0 ? ((lenv == L) ? keys[L - 1] : kNoKey)
+                   : (lenv + plenv >= L ? kth_of_two(keys, lenv, pkeys, plenv, L - 1) : kNoKey);
 
     // ---- a6 (warp 0): exact distance of the expanded node into the results
     if (warp == 0) {
@@ -1373,10 +1456,8 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     }
     __syncthreads();  // every warp's candidates and log entries are in
 
-    // ---- a9: sort the candidates (warp 0), rank them in the list, move the
-    // list's tail right in rounds of W blocks (all reads of a round before
-    // its writes; entries only move right, so the rounds run top-down), then
-    // drop the candidates into their places; entries pushed past L fall off
+    // ---- a9: sort the candidates (warp 0), then merge them into the list
+    // (all warps), or, for long lists, into the pending buffer (warp 0)
     const int c = ctl->cand_count;
     if (c > 0) {
       if (warp == 0) {
@@ -1396,46 +1477,35 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
         }
       }
       __syncthreads();
-      for (int j = tid; j < c; j += 32 * W) rank[j] = lower_bound_u64(keys, lenv, cand[j]);
-      __syncthreads();
-      const int pos0 = rank[0];
-      constexpr int kB = 256;  // entries per warp per round (8 per lane)
-      const int top_block = ((lenv - 1) / kB) * kB;
-      const int low_block = (pos0 / kB) * kB;
-      for (int r0 = top_block; r0 >= low_block; r0 -= W * kB) {
-        const int b = r0 - warp * kB;
-        unsigned long long kv[8];
-        unsigned char fv[8];
-        int np[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int i = b + t * 32 + lane;
-          const bool live = b >= low_block && i >= pos0 && i < lenv;
-          kv[t] = live ? keys[i] : 0ull;
-          fv[t] = live ? flags[i] : 0;
-          np[t] = !live ? L : (i >= rank[c - 1] ? i + c : i + upper_bound_i32(rank, c, i));
+      if (!lazy) {
+        const int pos0 = wg_merge(cand, nullptr, c, lenv);
+        if (warp == 0) {
+          len = (lenv + c < L) ? lenv + c : L;
+          if (pos0 < first_open) first_open = pos0;
         }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          if (np[t] < L) {
-            keys[np[t]] = kv[t];
-            flags[np[t]] = fv[t];
+      } else {
+        if (plenv + c > kPend) {
+          // the pending buffer is full: all warps merge it, selected flags
+          // and all, into the list (entries past rank L fall off)
+          const int pos0 = wg_merge(pkeys, pflags, plenv, lenv);
+          if (warp == 0) {
+            len = (lenv + plenv < L) ? lenv + plenv : L;
+            if (pos0 < first_open) first_open = pos0;
+            plen = 0;
+            pfirst_open = 0;
           }
         }
-        __syncthreads();
-      }
-      for (int j = tid; j < c; j += 32 * W) {
-        const int p = j + rank[j];
-        if (p < L) {
-          keys[p] = cand[j];
-          flags[p] = 0;
+        if (warp == 0) {
+          // this step's candidates into the pending buffer (one warp)
+          QueryState pend;
+          pend.keys = pkeys;
+          pend.flags = pflags;
+          pend.rank = rank;
+          pend.len = plen;
+          const int pchanged = merge_candidates(pend, cand, c, kPend, lane);
+          plen = pend.len;
+          if (pchanged < pfirst_open) pfirst_open = pchanged;
         }
-      }
-      __syncthreads();
-      if (warp == 0) {
-        len = (lenv + c < L) ? lenv + c : L;
-        if (pos0 < first_open) first_open = pos0;
       }
     }
     if (warp == 0 && steps >= max_steps) status = ANN_ENOMEM;  // cannot happen (each node expands once)

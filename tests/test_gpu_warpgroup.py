@@ -1,8 +1,9 @@
 """A warp group per query (ann_set_warps_per_query): 2 or 4 warps share one
 query's lookup table, list, fetch ring and visited set; warp 0 keeps the
 relaxed pipeline and the warps split each expansion's neighbours and the list
-merge.  The schedule is the single warp's, so ids, distances and per-query
-step counts must equal the oracle's bit for bit, at every depth."""
+merge (for long lists, the merge of a pending buffer).  The schedule is the
+single warp's, so ids, distances and per-query step counts must equal the
+oracle's bit for bit, at every depth."""
 import numpy as np
 import pytest
 
@@ -55,6 +56,45 @@ def test_warp_group_k_and_L_extremes(u8_pq, pq_index, W, k, L):
         pq_index.set_warps_per_query(1)
     oi, od, os_ = _oracle(u8_pq, k, L, 1, q=q)
     assert np.array_equal(ids, oi) and np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
+@pytest.mark.parametrize("W", [2, 4])
+@pytest.mark.parametrize("L", [2048, 4096, 8192])
+@pytest.mark.parametrize("depth", [0, 1, 2, 4])
+def test_warp_group_long_lists_bit_exact(u8_pq, pq_index, W, L, depth):
+    """From L = 2048 on the group keeps a pending buffer in front of the list
+    (warp 0 merges each step's candidates into it, all warps merge it into
+    the list when full); selection and the entry bound work on the union."""
+    q = u8_pq["q"][:40]
+    pq_index.set_warps_per_query(W)
+    try:
+        ids, dists, _, tr = pq_index.search(q, 10, L, depth, trace=True)
+    finally:
+        pq_index.set_warps_per_query(1)
+    oi, od, os_ = _oracle(u8_pq, 10, L, depth, q=q)
+    assert np.array_equal(ids, oi) and np.array_equal(dists.astype(np.float64), od)
+    assert np.array_equal(tr["steps"], os_)
+
+
+@pytest.mark.parametrize("R", [128])
+@pytest.mark.parametrize("W", [2, 4])
+def test_warp_group_long_lists_degree_128(u8_pq, R, W):
+    """Degree 128 (up to 128 entering candidates a step, the pending buffer's
+    size) with a long list."""
+    w = u8_pq
+    n = 6000
+    base = w["base"][:n]
+    codes = np.ascontiguousarray(w["codes"][:n])
+    adj = datagen.random_links(3, n, R)
+    ix = ann.Index(base, adj, 11, w["cb"], codes, tier=ann.ANN_TIER_HOST_PINNED)
+    try:
+        ix.set_warps_per_query(W)
+        ids, d, _, tr = ix.search(w["q"][:32], 10, 2560, 2, trace=True)
+    finally:
+        ix.close()
+    oi, od, os_ = _oracle(w, 10, 2560, 2, q=w["q"][:32], adj=adj, base=base, codes=codes, entry=11)
+    assert np.array_equal(ids, oi) and np.array_equal(d.astype(np.float64), od)
     assert np.array_equal(tr["steps"], os_)
 
 
