@@ -44,9 +44,9 @@ DATA = os.path.join(ROOT, "_data")
 # tier, which bounds the kernels) and DRAM read + write bytes, for each kernel
 # instance the benchmark can pick.
 NCU_BYTES_PER_EXPANSION = {
-    "search_kernel<PQ,2>": (420.0, 473.8),             # one warp per query, depth 1
-    "search_kernel<PQ,2,prefetch>": (420.0, 475.8),    # depth >= 2, next-node prefetch
-    "search_kernel_wg<2,4>": (420.0, 470.1),           # a warp group of 4 per query
+    "search_kernel<PQ,2>": (420.0, 467.2),             # one warp per query, depth 1
+    "search_kernel<PQ,2,prefetch>": (420.0, 480.6),    # depth >= 2, next-node prefetch
+    "search_kernel_wg<2,4>": (420.0, 464.8),           # a warp group of 4 per query
 }
 METRIC = "QPS at recall@10>=0.95 on 1 B300, relaxed vs sync search; p50/p99 latency"
 WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Vamana R=64, PQ M=32 in HBM, 512 B node blocks in host pinned memory, k=10"
