@@ -151,24 +151,27 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 // ---------------------------------------------------------------------------
 // Tensor-core path (uint8 data, d <= 128).
 //
-// distance(q, x) = |q|^2 + |x|^2 - 2 q.x.  The dot products of a tile of 128
-// queries (A, the MMA's M) with a tile of 128 base rows (B, its N) over the
-// d coordinates (K) run on tcgen05.mma (kind::f16, BF16 operands, FP32
-// accumulator in tensor memory).  uint8 values are exact in BF16, every
-// product is an integer below 2^16 and every partial sum an integer below
-// d * 255^2 <= 8,323,200 < 2^24, so FP32 accumulation is exact in any order;
-// the distance, below 2 * 8,323,200 < 2^24, is exact in FP32 as well.  The
-// top-k selection runs in the same kernel on the accumulator, so the
-// distance matrix never goes to HBM.
+// distance(q, x) = |q|^2 + v(q, x) with v = |x|^2 - 2 q.x; a query's ranking
+// depends on v alone.  v is one dot product over K = d + 16 coordinates:
+//   A row (query q): q_1 .. q_d, then 2^16, 2^8, 1, zeros;
+//   B row (base x):  -2 x_1 .. -2 x_d, then the base-256 digits of |x|^2
+//                    (|x|^2 >> 16, its middle byte, its low byte), zeros.
+// Every operand is an integer of at most 8 significant bits or a power of
+// two, so exact in BF16; every product and partial sum is an integer of
+// magnitude below 2 * 128 * 255^2 = 16,646,400 < 2^24, so FP32 accumulation
+// in tensor memory (tcgen05.mma, kind::f16) is exact in any order, and so is
+// the distance v + |q|^2 <= 8,323,200.  The first d coordinates are 64-wide
+// atoms in the 128-byte swizzled layout; the last 16 are one 32-byte-swizzled
+// tile, one more MMA per tile.  The top-k selection runs in the same kernel
+// on the accumulator, so the distance matrix never goes to HBM.
 //
 // Per CTA (two query tiles x a contiguous range of base tiles), 20 warps:
 //   warp 0 (one lane)  TMA producer: the two query tiles once, then base
 //                      tiles into a ring of kTcStages shared-memory stages
-//                      (128-byte swizzled, one 64-coordinate "atom" = 128 B
-//                      per row), and each tile's 128 base norms (a bulk copy)
-//                      into a ring of kNormRing slots;
-//   warp 1 (one lane)  MMA issuer: for each base tile, d/16 MMAs per query
-//                      tile into one of two accumulator pairs (4 x 128
+//                      (each: the 64-coordinate atoms, 128 B per row, and
+//                      the 16-coordinate tail, 32 B per row);
+//   warp 1 (one lane)  MMA issuer: for each base tile, d/16 + 1 MMAs per
+//                      query tile into one of two accumulator pairs (4 x 128
 //                      tensor-memory columns, all 512); tcgen05.commit frees
 //                      the stage and publishes the pair;
 //   warps 4-19         four epilogue warpgroups, one per accumulator (query
@@ -176,19 +179,20 @@ __global__ void __launch_bounds__(256) topk_merge(const unsigned long long* __re
 //                      32*(w%4)+t of its query tile with tcgen05.ld and keeps
 //                      that query's ascending top-k of (distance, id) keys.
 // Two query tiles share each base tile, which halves the base's L2 traffic.
-// The epilogue works on v = |x|^2 - 2 q.x (the query's own |q|^2 is a
-// constant of its ranking) against the bound k-th distance - |q|^2: one FMA
-// per distance and a tree of 3-input mins, then one compare per 32 columns;
+// The epilogue takes v straight from the accumulator: a tree of 3-input mins
+// per 32 columns and one compare against the bound k-th distance - |q|^2;
 // only a lane whose minimum is within the bound looks at its candidates one
 // by one (after the first tiles, the common case is that none is).  The next
 // 32 columns load from tensor memory while the current ones are scanned, and
 // the accumulator goes back to the MMA as soon as its last columns are in
-// registers.  Base norms are padded to whole tiles with +inf, so rows past
-// the end never qualify.  The bound starts at the running k-th best of the
-// chunks already folded, and the CTAs of a query share a distance bound in
-// global memory: each lowers it (atomicMin) to its own k-th distance and
-// reads it once per tile (a tile ahead), so a CTA's first tiles no longer
-// admit a stream of candidates that another CTA has already ruled out.
+// registers.  Rows past the end of the base have zero coordinates and the
+// largest norm digits (v = 16,777,215 exceeds every real bound), and the
+// candidate path checks the row index as well.  The bound starts at the
+// running k-th best of the chunks already folded, and the CTAs of a query
+// share a distance bound in global memory: each lowers it (atomicMin) to its
+// own k-th distance and reads it once per tile (a tile ahead), so a CTA's
+// first tiles no longer admit a stream of candidates that another CTA has
+// already ruled out.
 // Each warpgroup writes its lists as one part; a fold kernel merges the parts
 // with the running top-k after each chunk of the base.  The first chunk is
 // small, so that the running top-k bounds every later chunk from its start.
@@ -200,16 +204,16 @@ constexpr int kTcM = 128;            // queries per CTA (MMA M)
 constexpr int kTcN = 128;            // base rows per tile (MMA N)
 constexpr int kTcQT = 2;             // query tiles per CTA
 constexpr int kTcStages = 3;         // base-tile ring
-constexpr int kNormRing = 8;         // base-norm slots (one tile each)
-static_assert(kNormRing >= kTcStages + 2, "a norm slot is reused only after its tile's epilogue");
 constexpr int kAtomBytes = 128 * 128;  // one 64-coordinate BF16 atom of a 128-row tile
+constexpr int kTailBytes = 128 * 32;   // the 16-coordinate tail of a 128-row tile
+constexpr int kTail = 16;              // tail coordinates: norm digits or their weights
 constexpr int kTcThreads = 128 + 4 * 128;
 constexpr long long kTcWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 struct TcArgs {
   const float* qn;          // [nq] query norms
-  const float* xn;          // [tiles * 128] base-row norms of this chunk, +inf past its rows
   int64_t nq;
+  int32_t chunk_n;          // rows of this chunk
   int64_t id0;              // id of the chunk's first row
   int32_t tiles;            // base tiles in the chunk
   int32_t splits;           // CTAs per query tile
@@ -309,6 +313,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The same for a 32-byte-swizzled K-major tile (rows of 32 bytes = one
+// 16-coordinate MMA step, 8-row groups 256 bytes apart), swizzle mode 6.
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;           // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(256 >> 4) << 32;    // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;           // version
+  d |= static_cast<uint64_t>(6) << 61;           // 32-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -364,14 +380,6 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : ANN_R32_INOUT(r) : : "memory");
 }
 
-// Plain (untiled) bulk copy global -> shared, completing on an mbarrier.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(sh_u32(dst)), "l"(src), "r"(bytes), "r"(sh_u32(bar))
-      : "memory");
-}
-
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -379,23 +387,24 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-    knn_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
+    knn_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap qtail,
+                  const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xtail,
                   TcArgs a) {
   extern __shared__ unsigned char tc_smem_raw[];
   // 1024-byte alignment for the swizzled operand tiles
   const uint32_t raw = sh_u32(tc_smem_raw);
   unsigned char* smem = tc_smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   unsigned char* sA = smem;                                   // kTcQT x 2 atoms x 16 KB
-  unsigned char* sB = smem + kTcQT * 2 * kAtomBytes;          // kTcStages x 2 atoms x 16 KB
-  float* sN = reinterpret_cast<float*>(sB + kTcStages * 2 * kAtomBytes);  // kNormRing x 128 base norms
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sN + kNormRing * kTcN);
+  unsigned char* sB = sA + kTcQT * 2 * kAtomBytes;            // kTcStages x 2 atoms x 16 KB
+  unsigned char* sAt = sB + kTcStages * 2 * kAtomBytes;       // kTcQT tails x 4 KB
+  unsigned char* sBt = sAt + kTcQT * kTailBytes;              // kTcStages tails x 4 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sBt + kTcStages * kTailBytes);
   uint64_t* full = bars;                    // [kTcStages]
   uint64_t* empty = bars + kTcStages;       // [kTcStages]
   uint64_t* a_full = bars + 2 * kTcStages;  // [1]
   uint64_t* acc_full = a_full + 1;          // [2]
   uint64_t* acc_empty = a_full + 3;         // [2]
-  uint64_t* n_full = a_full + 5;            // [kNormRing]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(n_full + kNormRing);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 5);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -416,7 +425,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(acc_full + 1, 1);
     mbar_init(acc_empty + 0, 4 * kTcQT);  // the warps of the kTcQT warpgroups of a buffer
     mbar_init(acc_empty + 1, 4 * kTcQT);
-    for (int i = 0; i < kNormRing; ++i) mbar_init(n_full + i, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -431,33 +439,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int dp = natoms * 64;  // x coordinate of the tail
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
     asm volatile("prefetch.tensormap [%0];" ::"l"(&qmap) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&qtail) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&xmap) : "memory");
-    mbar_expect_tx(a_full, kTcQT * natoms * kAtomBytes);
-    for (int qt = 0; qt < kTcQT; ++qt)
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&xtail) : "memory");
+    mbar_expect_tx(a_full, kTcQT * (natoms * kAtomBytes + kTailBytes));
+    for (int qt = 0; qt < kTcQT; ++qt) {
+      const int row = static_cast<int>(q0 + qt * kTcM);
       for (int at = 0; at < natoms; ++at)
-        tma_load_2d(sA + (qt * 2 + at) * kAtomBytes, &qmap, a_full, 64 * at,
-                    static_cast<int>(q0 + qt * kTcM));
+        tma_load_2d(sA + (qt * 2 + at) * kAtomBytes, &qmap, a_full, 64 * at, row);
+      tma_load_2d(sAt + qt * kTailBytes, &qtail, a_full, dp, row);
+    }
     int issued = 0;
     bool ok = true;
     for (int i = 0; i < my_tiles && ok; ++i) {
       const int st = i % kTcStages;
       const uint32_t ph = (i / kTcStages) & 1;
       if (!mbar_wait(empty + st, ph ^ 1u, abort)) { ok = false; break; }
-      mbar_expect_tx(full + st, natoms * kAtomBytes);
+      mbar_expect_tx(full + st, natoms * kAtomBytes + kTailBytes);
       const int row = (t_lo + i) * kTcN;
       for (int at = 0; at < natoms; ++at)
         tma_load_2d(sB + (st * 2 + at) * kAtomBytes, &xmap, full + st, 64 * at, row);
-      // the tile's 128 base norms.  Slot i % kNormRing was last read by the
-      // epilogue of tile i - kNormRing, which finished before the MMA of
-      // tile i - kNormRing + 2 began; that MMA is at or before the MMA of
-      // tile i - kTcStages, whose completion freed the stage above.
-      const int ns = i % kNormRing;
-      mbar_expect_tx(n_full + ns, kTcN * 4);
-      bulk_load(sN + ns * kTcN, a.xn + row, kTcN * 4, n_full + ns);
+      tma_load_2d(sBt + st * kTailBytes, &xtail, full + st, dp, row);
       issued = i + 1;
     }
     if (!ok) {
@@ -465,14 +472,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_drain(a_full, 0);
       for (int i = issued - kTcStages < 0 ? 0 : issued - kTcStages; i < issued; ++i)
         mbar_drain(full + (i % kTcStages), (i / kTcStages) & 1);
-      for (int i = issued - kNormRing < 0 ? 0 : issued - kNormRing; i < issued; ++i)
-        mbar_drain(n_full + (i % kNormRing), (i / kNormRing) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     if (mbar_wait(a_full, 0, abort)) {
       tc_fence_after();
-      const uint32_t a_base = sh_u32(sA);
+      const uint32_t a_base = sh_u32(sA), at_base = sh_u32(sAt);
       for (int i = 0; i < my_tiles; ++i) {
         const int st = i % kTcStages;
         const uint32_t ph = (i / kTcStages) & 1;
@@ -482,6 +487,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!mbar_wait(full + st, ph, abort)) break;
         tc_fence_after();
         const uint32_t b_base = sh_u32(sB + st * 2 * kAtomBytes);
+        const uint32_t bt = sh_u32(sBt + st * kTailBytes);
         for (int qt = 0; qt < kTcQT; ++qt) {
           const uint32_t d_tmem = tmem + static_cast<uint32_t>((b * kTcQT + qt) * kTcN);
           const uint32_t aq = a_base + static_cast<uint32_t>(qt * 2 * kAtomBytes);
@@ -493,6 +499,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const uint64_t bd = sw128_desc(b_base + at * kAtomBytes) + static_cast<uint64_t>(2 * kk);
               tc_mma(d_tmem, ad, bd, (at | kk) != 0);
             }
+          // the tail: |x|^2's digits times their weights
+          tc_mma(d_tmem, sw32_desc(at_base + static_cast<uint32_t>(qt * kTailBytes)), sw32_desc(bt), 1u);
         }
         tc_commit(empty + st);
         tc_commit(acc_full + b);
@@ -514,8 +522,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // k-th best of the chunks folded so far (keys are distinct: ids differ),
     // and the shared per-query distance bound, which every CTA lowers to its
     // own k-th distance (k keys of one range at or below it mean no key
-    // above it is in the final k).  thr_f is the same bound on
-    // v = |x|^2 - 2 q.x; a row past the query count never qualifies.
+    // above it is in the final k).  thr_f is the same bound on v; a row past
+    // the query count never qualifies.
     unsigned long long thr =
         live ? a.keys[static_cast<size_t>(gq) * a.nslots * k + (k - 1)] : 0ull;
     float thr_f = !live ? -FLT_MAX
@@ -531,40 +539,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t taddr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                            static_cast<uint32_t>((b * kTcQT + qt) * kTcN);
 
-    // 32 columns: v = |x|^2 - 2 q.x, a tree of 3-input mins, and only if the
-    // minimum is within the bound, the lane's candidates one by one
-    auto scan = [&](const uint32_t (&r)[32], const float* nrm, int j0) {
-      float v[32];
-#pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        const float4 nv = reinterpret_cast<const float4*>(nrm)[g];
-        v[4 * g + 0] = fmaf(-2.f, __uint_as_float(r[4 * g + 0]), nv.x);
-        v[4 * g + 1] = fmaf(-2.f, __uint_as_float(r[4 * g + 1]), nv.y);
-        v[4 * g + 2] = fmaf(-2.f, __uint_as_float(r[4 * g + 2]), nv.z);
-        v[4 * g + 3] = fmaf(-2.f, __uint_as_float(r[4 * g + 3]), nv.w);
-      }
+    // 32 columns of v: a tree of 3-input mins, and only if the minimum is
+    // within the bound, the lane's candidates one by one
+    auto scan = [&](const uint32_t (&r)[32], int j0) {
       float p[8];
 #pragma unroll
-      for (int g = 0; g < 8; ++g) p[g] = min3f(v[4 * g], v[4 * g + 1], fminf(v[4 * g + 2], v[4 * g + 3]));
+      for (int g = 0; g < 8; ++g)
+        p[g] = min3f(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]),
+                     fminf(__uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3])));
       const float m = min3f(min3f(p[0], p[1], p[2]), min3f(p[3], p[4], p[5]), fminf(p[6], p[7]));
       if (m > thr_f) return;  // the common case: nothing within the bound
       unsigned cm = 0u;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) cm |= static_cast<unsigned>(v[j] <= thr_f) << j;
+      for (int j = 0; j < 32; ++j) cm |= static_cast<unsigned>(__uint_as_float(r[j]) <= thr_f) << j;
       while (cm) {
         const int j = __ffs(cm) - 1;
         cm &= cm - 1u;
-        // v[j] for a run-time j without local memory: a select tree on j's bits
-        float t16[16], t8[8], t4[4], t2[2];
+        if (j0 + j >= a.chunk_n) break;  // rows past the end (the rest are too)
+        // r[j] for a run-time j without local memory: a select tree on j's bits
+        uint32_t t16[16], t8[8], t4[4], t2[2];
 #pragma unroll
-        for (int x = 0; x < 16; ++x) t16[x] = (j & 1) ? v[2 * x + 1] : v[2 * x];
+        for (int x = 0; x < 16; ++x) t16[x] = (j & 1) ? r[2 * x + 1] : r[2 * x];
 #pragma unroll
         for (int x = 0; x < 8; ++x) t8[x] = (j & 2) ? t16[2 * x + 1] : t16[2 * x];
 #pragma unroll
         for (int x = 0; x < 4; ++x) t4[x] = (j & 4) ? t8[2 * x + 1] : t8[2 * x];
 #pragma unroll
         for (int x = 0; x < 2; ++x) t2[x] = (j & 8) ? t4[2 * x + 1] : t4[2 * x];
-        const float vj = (j & 16) ? t2[1] : t2[0];
+        const float vj = __uint_as_float((j & 16) ? t2[1] : t2[0]);
         if (vj > thr_f) continue;  // the bound tightened after the mask was taken
         // v and |q|^2 are integers below 2^24: the sum is the exact distance
         const unsigned dist = __float2uint_rn(vj + qn);
@@ -597,12 +599,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     unsigned next_bound = live ? __ldcg(a.bound + gq) : ~0u;
     for (int i = b; i < my_tiles; i += 2) {
       const uint32_t u = static_cast<uint32_t>(i >> 1);
-      const int ns = i % kNormRing;
       // one lane waits, so the warp stays converged for tcgen05.ld
       int ok = 1;
-      if (lane == 0)
-        ok = (mbar_wait(acc_full + b, u & 1u, abort) &&
-              mbar_wait(n_full + ns, static_cast<uint32_t>(i / kNormRing) & 1u, abort)) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(acc_full + b, u & 1u, abort) ? 1 : 0;
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       tc_fence_after();
       if (live) {
@@ -610,7 +609,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         next_bound = __ldcg(a.bound + gq);
       }
       const int col0 = (t_lo + i) * kTcN;
-      const float* nrm = sN + ns * kTcN;
       // the next 32 columns load while the current ones are scanned; the
       // accumulator goes back to the MMA once its last columns are in
       // registers
@@ -618,18 +616,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tmem_ld32_async(taddr, r0);
       tmem_wait(r0);
       tmem_ld32_async(taddr + 32u, r1);
-      scan(r0, nrm, col0);
+      scan(r0, col0);
       tmem_wait(r1);
       tmem_ld32_async(taddr + 64u, r0);
-      scan(r1, nrm + 32, col0 + 32);
+      scan(r1, col0 + 32);
       tmem_wait(r0);
       tmem_ld32_async(taddr + 96u, r1);
-      scan(r0, nrm + 64, col0 + 64);
+      scan(r0, col0 + 64);
       tmem_wait(r1);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty + b);
-      scan(r1, nrm + 96, col0 + 96);
+      scan(r1, col0 + 96);
     }
     if (live) {
       unsigned long long* out =
@@ -648,25 +646,62 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// uint8 rows -> BF16 rows zero-padded to dp coordinates, and each row's
-// squared norm (an exact integer in FP32).  Rows in [rows, rows_pad) are
-// zero with norm +inf.  One warp per row.
-__global__ void to_bf16_rows(const uint8_t* __restrict__ x, int64_t rows, int64_t rows_pad, int d, int dp,
-                             uint16_t* __restrict__ out, float* __restrict__ norms) {
+// BF16 of a small integer or power of two (exact: at most 8 significant bits).
+__device__ __forceinline__ uint16_t bf16_exact(float v) {
+  return static_cast<uint16_t>(__float_as_uint(v) >> 16);
+}
+
+// Base rows -> BF16 B rows of w = dp + kTail coordinates: -2 x_1 .. -2 x_d,
+// zeros to dp, then the base-256 digits of |x|^2 (high, middle, low) and
+// zeros.  Rows in [rows, rows_pad) get zero coordinates and digits 255, 255,
+// 255: v = 2^24 - 1, above every real v.  One warp per row.
+__global__ void base_rows_bf16(const uint8_t* __restrict__ x, int64_t rows, int64_t rows_pad, int d, int dp,
+                               uint16_t* __restrict__ out) {
   const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows_pad) return;
   const bool real = r < rows;
   const uint8_t* src = x + (real ? r : 0) * d;
-  uint16_t* dst = out + r * dp;
+  const int w = dp + kTail;
+  uint16_t* dst = out + r * w;
   unsigned sq = 0;
   for (int j = lane; j < dp; j += 32) {
     const unsigned v = (real && j < d) ? src[j] : 0u;
     sq += v * v;
-    dst[j] = static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);  // exact
+    dst[j] = bf16_exact(-2.f * static_cast<float>(v));
   }
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if (lane == 0) norms[r] = real ? static_cast<float>(sq) : __int_as_float(0x7f800000);
+  if (lane < kTail) {
+    unsigned digit = 0;
+    if (lane < 3) digit = real ? (sq >> (8 * (2 - lane))) & 0xffu : 0xffu;
+    dst[dp + lane] = bf16_exact(static_cast<float>(digit));
+  }
+}
+
+// Query rows -> BF16 A rows: q_1 .. q_d, zeros to dp, then the digit weights
+// 2^16, 2^8, 1 and zeros; and each row's squared norm (an exact integer in
+// FP32).  Rows in [rows, rows_pad) are zero.  One warp per row.
+__global__ void query_rows_bf16(const uint8_t* __restrict__ q, int64_t rows, int64_t rows_pad, int d, int dp,
+                                uint16_t* __restrict__ out, float* __restrict__ norms) {
+  const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows_pad) return;
+  const bool real = r < rows;
+  const uint8_t* src = q + (real ? r : 0) * d;
+  const int w = dp + kTail;
+  uint16_t* dst = out + r * w;
+  unsigned sq = 0;
+  for (int j = lane; j < dp; j += 32) {
+    const unsigned v = (real && j < d) ? src[j] : 0u;
+    sq += v * v;
+    dst[j] = bf16_exact(static_cast<float>(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane < kTail) {
+    const float wt = (real && lane < 3) ? static_cast<float>(1u << (8 * (2 - lane))) : 0.f;
+    dst[dp + lane] = bf16_exact(wt);
+  }
+  if (lane == 0) norms[r] = static_cast<float>(sq);
 }
 
 // Merge the parts of every query into its running top-k (slot 0) and clear
@@ -705,22 +740,24 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map of `rows` BF16 rows of dp coordinates, 64 x 128 boxes, 128-byte
-// swizzle; rows past the end read as zero.
-bool bf16_row_map(CUtensorMap* m, const void* ptr, int64_t rows, int dp) {
+// 2-D map of `rows` BF16 rows of `w` coordinates with box_x x 128 boxes:
+// 64-coordinate boxes in the 128-byte swizzle for the atoms, 16-coordinate
+// boxes in the 32-byte swizzle for the tail.  Every box the kernel loads lies
+// inside the buffer.
+bool bf16_row_map(CUtensorMap* m, const void* ptr, int64_t rows, int w, int box_x, bool tail) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(dp), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(dp) * 2};
-  cuuint32_t box[2] = {64, 128};
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(w), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(w) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_x), 128};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, tail ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr size_t kTcSmem =
-    1024 + kTcQT * 2 * kAtomBytes + kTcStages * 2 * kAtomBytes + kNormRing * kTcN * 4 + 256;
+constexpr size_t kTcSmem = 1024 + kTcQT * 2 * kAtomBytes + kTcStages * 2 * kAtomBytes + kTcQT * kTailBytes +
+                           kTcStages * kTailBytes + 256;
 
 }  // namespace
 
@@ -758,18 +795,18 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
   }
   const int nslots = 1 + 2 * splits;
   uint16_t *qb = nullptr, *xb = nullptr;
-  float *qn = nullptr, *xn = nullptr;
+  float* qn = nullptr;
   unsigned long long* keys = nullptr;
   unsigned* bound = nullptr;
   int* err = nullptr;
-  // row buffers padded to whole boxes (zero rows, +inf norms), so every TMA
-  // box lies inside its buffer
+  // row buffers of w = dp + kTail coordinates, padded to whole boxes (see
+  // base_rows_bf16 / query_rows_bf16), so every TMA box lies inside them
+  const int w = dp + kTail;
   const int64_t q_rows = qblocks * kTcQT * kTcM;
   const int64_t x_rows = static_cast<int64_t>(max_tiles) * kTcN;
-  cudaError_t e = cudaMalloc(&qb, static_cast<size_t>(q_rows) * dp * 2);
+  cudaError_t e = cudaMalloc(&qb, static_cast<size_t>(q_rows) * w * 2);
   if (e == cudaSuccess) e = cudaMalloc(&qn, static_cast<size_t>(q_rows) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&xb, static_cast<size_t>(x_rows) * dp * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&xn, static_cast<size_t>(x_rows) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&xb, static_cast<size_t>(x_rows) * w * 2);
   if (e == cudaSuccess) e = cudaMalloc(&keys, static_cast<size_t>(nq) * nslots * k * 8);
   if (e == cudaSuccess) e = cudaMalloc(&bound, static_cast<size_t>(nq) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
@@ -778,13 +815,15 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
   if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, static_cast<size_t>(nq) * nslots * k * 8, stream);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTcSmem));
-  CUtensorMap qmap, xmap;
+  CUtensorMap qmap, qtail, xmap, xtail;
   if (e == cudaSuccess) {
-    to_bf16_rows<<<static_cast<unsigned>((q_rows * 32 + 255) / 256), 256, 0, stream>>>(queries, nq, q_rows, d, dp,
-                                                                                     qb, qn);
+    query_rows_bf16<<<static_cast<unsigned>((q_rows * 32 + 255) / 256), 256, 0, stream>>>(queries, nq, q_rows, d,
+                                                                                        dp, qb, qn);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && !bf16_row_map(&qmap, qb, q_rows, dp)) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess && (!bf16_row_map(&qmap, qb, q_rows, w, 64, false) ||
+                           !bf16_row_map(&qtail, qb, q_rows, w, kTail, true)))
+    e = cudaErrorInvalidValue;
   // The first chunk is small (2^17 rows): once it is folded, every query's
   // running k-th best over it bounds the keys of all later chunks, so their
   // CTAs start with a tight bound instead of each warming up its own.
@@ -793,16 +832,16 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
     const int64_t cmax = c0 == 0 ? seed_rows : chunk;
     const int64_t cn = (n - c0 < cmax) ? n - c0 : cmax;
     const int64_t map_rows = (cn + kTcN - 1) / kTcN * kTcN;
-    to_bf16_rows<<<static_cast<unsigned>((map_rows * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn,
-                                                                                       map_rows, d, dp, xb, xn);
-    if (!bf16_row_map(&xmap, xb, map_rows, dp)) {
+    base_rows_bf16<<<static_cast<unsigned>((map_rows * 32 + 255) / 256), 256, 0, stream>>>(base + c0 * d, cn,
+                                                                                         map_rows, d, dp, xb);
+    if (!bf16_row_map(&xmap, xb, map_rows, w, 64, false) || !bf16_row_map(&xtail, xb, map_rows, w, kTail, true)) {
       e = cudaErrorInvalidValue;
       break;
     }
     TcArgs ta;
     ta.qn = qn;
-    ta.xn = xn;
     ta.nq = nq;
+    ta.chunk_n = static_cast<int32_t>(cn);
     ta.id0 = c0;
     ta.tiles = static_cast<int32_t>((cn + kTcN - 1) / kTcN);
     ta.splits = splits < ta.tiles ? splits : ta.tiles;
@@ -813,7 +852,7 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
     ta.bound = bound;
     ta.error = err;
     knn_tc_kernel<<<dim3(static_cast<unsigned>(qblocks), static_cast<unsigned>(ta.splits)), kTcThreads, kTcSmem,
-                    stream>>>(qmap, xmap, ta);
+                    stream>>>(qmap, qtail, xmap, xtail, ta);
     topk_fold<<<static_cast<unsigned>(nq), 256, 0, stream>>>(keys, nslots, k);
     e = cudaGetLastError();
     c0 += cn;
@@ -830,7 +869,6 @@ cudaError_t knn_exact_tc(const uint8_t* base, int64_t n, int d, const uint8_t* q
   cudaFree(qb);
   cudaFree(qn);
   cudaFree(xb);
-  cudaFree(xn);
   cudaFree(keys);
   cudaFree(bound);
   cudaFree(err);
