@@ -397,6 +397,27 @@ int ann_reorder_graph(const void* base, int32_t dtype, int64_t n, int32_t d, int
                       void* base_out, int32_t* adj_out, uint8_t* codes_out,
                       int32_t* old_of_new, int32_t* entry_out);
 
+/* Storage orders of ann_reorder_graph_ex. */
+typedef enum {
+  ANN_ORDER_BFS = 0,     /* breadth-first from the entry node (ann_reorder_graph) */
+  ANN_ORDER_SPATIAL = 1  /* leaves of a 2-means bisection tree of the vectors, 128 nodes each */
+} ann_order;
+
+/*
+ * ann_reorder_graph with a choice of order.  ANN_ORDER_SPATIAL splits the
+ * vectors recursively in two by 2-means (two seed points from a hash of the
+ * range, three rounds of Lloyd's step, the larger margins first, ties by id)
+ * into parts whose sizes are multiples of 128, down to leaves of at most 128
+ * nodes: 128 node blocks of 512 bytes fill one 64 KB translation granule, and
+ * a query's successive expansions, which stay near the query in space, fall
+ * into few of them.  Deterministic; *entry_out is wherever the entry lands.
+ * Same outputs and errors as ann_reorder_graph otherwise.
+ */
+int ann_reorder_graph_ex(const void* base, int32_t dtype, int64_t n, int32_t d, int32_t R,
+                         const int32_t* adj, int32_t entry, const uint8_t* codes, int32_t M,
+                         int32_t order, void* base_out, int32_t* adj_out, uint8_t* codes_out,
+                         int32_t* old_of_new, int32_t* entry_out);
+
 /*
  * Build a Vamana graph (index-construction tooling; host threads).  Random
  * out-neighbours to start, then two passes (alpha 1, then `alpha`) of

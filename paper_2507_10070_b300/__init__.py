@@ -372,10 +372,12 @@ def encode_fp8e4m3(x, scale: float = 1.0):
     return out
 
 
-def reorder_graph(base, adj, entry: int, codes=None):
-    """Breadth-first storage order from the entry node (ann_reorder_graph).
-    Returns (base, adj, entry, codes, old_of_new) in the new order; load them
-    with id_map=old_of_new so that searches report the original ids."""
+def reorder_graph(base, adj, entry: int, codes=None, order: str = "bfs"):
+    """Storage order of the node blocks (ann_reorder_graph_ex): "bfs", breadth
+    first from the entry node, or "spatial", the leaves (128 nodes each) of a
+    2-means bisection tree of the vectors.  Returns (base, adj, entry, codes,
+    old_of_new) in the new order; load them with id_map=old_of_new so that
+    searches report the original ids."""
     base = _c(base)
     adj = _c(adj, np.int32)
     n, d = base.shape
@@ -387,9 +389,10 @@ def reorder_graph(base, adj, entry: int, codes=None):
     codes_out = None if codes is None else np.empty_like(codes)
     old_of_new = np.empty(n, np.int32)
     entry_out = ctypes.c_int32(0)
-    _check(_lib().ann_reorder_graph(_p(base), _dtype_code(base), n, d, R, _p(adj), int(entry),
-                                    _p(codes), M, _p(base_out), _p(adj_out), _p(codes_out),
-                                    _p(old_of_new), ctypes.byref(entry_out)))
+    od = {"bfs": _abi.ANN_ORDER_BFS, "spatial": _abi.ANN_ORDER_SPATIAL}[order]
+    _check(_lib().ann_reorder_graph_ex(_p(base), _dtype_code(base), n, d, R, _p(adj), int(entry),
+                                       _p(codes), M, od, _p(base_out), _p(adj_out), _p(codes_out),
+                                       _p(old_of_new), ctypes.byref(entry_out)))
     return base_out, adj_out, int(entry_out.value), codes_out, old_of_new
 
 

@@ -14,6 +14,7 @@ ANN_NAV_AUTO, ANN_NAV_BF16, ANN_NAV_FP8 = 0, 1, 2
 
 ANN_KNN_AUTO, ANN_KNN_TENSOR_CORES, ANN_KNN_CUDA_CORES = 0, 1, 2
 ANN_BUILD_AUTO, ANN_BUILD_TENSOR_CORES, ANN_BUILD_CUDA_CORES = 0, 1, 2
+ANN_ORDER_BFS, ANN_ORDER_SPATIAL = 0, 1
 
 STATUS_NAMES = {0: "ANN_OK", -1: "ANN_EINVAL", -2: "ANN_ENOMEM", -3: "ANN_ECUDA",
                 -4: "ANN_ETIMEOUT", -5: "ANN_EBUSY", -6: "ANN_EIO"}
@@ -29,7 +30,7 @@ EXPORTS = ["ann_last_error", "ann_version", "ann_load_graph", "ann_save_graph_fi
            "ann_serve_poll", "ann_serve_poll_any", "ann_serve_stats", "ann_serve_destroy",
            "ann_autotune_degree", "ann_build_graph_gpu", "ann_build_graph_gpu_ex", "ann_encode_bf16",
            "ann_encode_fp8e4m3",
-           "ann_pq_encode_gpu", "ann_reorder_graph"]
+           "ann_pq_encode_gpu", "ann_reorder_graph", "ann_reorder_graph_ex"]
 
 
 class AnnError(RuntimeError):
@@ -147,6 +148,9 @@ def lib():
         L.ann_encode_fp8e4m3.argtypes = [P, I64, ctypes.c_float, P]
         L.ann_reorder_graph.restype = ctypes.c_int
         L.ann_reorder_graph.argtypes = [P, I32, I64, I32, I32, P, I32, P, I32, P, P, P, P, P]
+        L.ann_reorder_graph_ex.restype = ctypes.c_int
+        L.ann_reorder_graph_ex.argtypes = [P, I32, I64, I32, I32, P, I32, P, I32, I32, P, P, P, P,
+                                           ctypes.POINTER(ctypes.c_int32)]
         L.ann_pq_encode_gpu.restype = ctypes.c_int
         L.ann_pq_encode_gpu.argtypes = [P, I32, I64, I32, I32, P, P]
         L.ann_set_warps_per_query.restype = ctypes.c_int

@@ -245,13 +245,14 @@ def test_id_map_relabels_results(u8_pq, pq_index, tmp_path):
     assert np.array_equal(b_i, _relabel(a_i, labels)) and np.array_equal(b_d, a_d)
 
 
+@pytest.mark.parametrize("order", ["bfs", "spatial"])
 @pytest.mark.parametrize("L,depth", [(64, 1), (256, 0)])
-def test_breadth_first_layout_matches_oracle(u8_pq, L, depth):
-    """The kernel on the breadth-first reordered index reports original ids
-    (through the id map) and equals the oracle searching the same reordered
-    index, mapped back the same way."""
+def test_reordered_layout_matches_oracle(u8_pq, order, L, depth):
+    """The kernel on the reordered index (breadth-first or spatial) reports
+    original ids (through the id map) and equals the oracle searching the
+    same reordered index, mapped back the same way."""
     w = u8_pq
-    b2, a2, e2, c2, old = ann.reorder_graph(w["base"], w["adj"], w["entry"], w["codes"])
+    b2, a2, e2, c2, old = ann.reorder_graph(w["base"], w["adj"], w["entry"], w["codes"], order=order)
     ix = ann.Index(b2, a2, e2, w["cb"], c2, tier=ann.ANN_TIER_HOST_PINNED, id_map=old)
     try:
         ids, d, _, tr = ix.search(w["q"], 10, L, depth, trace=True)

@@ -89,7 +89,8 @@ def test_reorder_graph_is_breadth_first_and_relabels():
         ann.reorder_graph(base, bad, 0, codes)
 
 
-def test_reordered_index_searches_the_same_graph():
+@pytest.mark.parametrize("order", ["bfs", "spatial"])
+def test_reordered_index_searches_the_same_graph(order):
     """The oracle on the reordered index, with ids mapped back, equals the
     oracle on the original (float32 data: no distance ties)."""
     mx = datagen.inmemory_f32()
@@ -97,11 +98,54 @@ def test_reordered_index_searches_the_same_graph():
     entry = oracle.medoid(base)
     adj = oracle.vamana(base, 32, 1.2, 64, entry, datagen.build_order(mx.seed, 4000),
                         datagen.random_out_neighbours(mx.seed, 4000, 32))
-    b2, a2, e2, _, old = ann.reorder_graph(base, adj, entry)
+    b2, a2, e2, _, old = ann.reorder_graph(base, adj, entry, order=order)
+    assert old[e2] == entry
     for depth in (0, 2):
         i0, d0, s0 = oracle.search(base, adj, entry, q, 10, 48, depth)
         i1, d1, s1 = oracle.search(b2, a2, e2, q, 10, 48, depth)
         assert np.array_equal(old[i1], i0) and np.array_equal(d1, d0) and np.array_equal(s1, s0)
+
+
+def test_spatial_order_relabels_and_groups_neighbours_in_space():
+    """The spatial order is a permutation that relabels rows, codes and ids
+    consistently, is deterministic, and puts points that are close in space
+    into the same 128-node leaves: within a leaf the mean squared distance is
+    a fraction of that between random points, and a point's nearest
+    neighbour shares its leaf far more often than chance."""
+    rng = np.random.default_rng(7)
+    n, R = 5000, 8
+    centres = rng.integers(0, 256, (40, 16))
+    base = np.clip(centres[rng.integers(0, 40, n)] + rng.normal(0, 12, (n, 16)), 0, 255).astype(np.uint8)
+    adj = rng.integers(0, n, (n, R)).astype(np.int32)
+    adj[rng.random((n, R)) < 0.2] = -1
+    codes = rng.integers(0, 256, (n, 4)).astype(np.uint8)
+    b2, a2, e2, c2, old = ann.reorder_graph(base, adj, 123, codes, order="spatial")
+    assert np.array_equal(np.sort(old), np.arange(n))
+    pos = np.empty(n, np.int64)
+    pos[old] = np.arange(n)
+    assert e2 == pos[123]
+    assert np.array_equal(b2, base[old]) and np.array_equal(c2, codes[old])
+    assert np.array_equal(a2, np.where(adj[old] >= 0, pos[np.maximum(adj[old], 0)], -1))
+    again = ann.reorder_graph(base, adj, 123, codes, order="spatial")
+    assert np.array_equal(again[4], old)
+    x = b2.astype(np.float64)
+    leaf = np.arange(n) // 128
+    within = np.mean([((x[leaf == l] - x[leaf == l].mean(0)) ** 2).sum(1).mean() for l in range(leaf.max())])
+    overall = ((x - x.mean(0)) ** 2).sum(1).mean()
+    assert within < 0.25 * overall
+    sample = rng.choice(n, 300, replace=False)
+    dd = ((x[sample][:, None, :] - x[None, :, :]) ** 2).sum(-1)
+    dd[np.arange(300), sample] = np.inf
+    nn = dd.argmin(1)
+    same_leaf = np.mean(leaf[sample] == leaf[nn])
+    assert same_leaf > 0.3 and same_leaf > 10 * (128 / n)
+    # an unknown order is rejected
+    import ctypes
+    e_out = ctypes.c_int32(0)
+    rc = ann._lib().ann_reorder_graph_ex(ann._p(base), 0, n, 16, R, ann._p(adj), 0, None, 0, 7,
+                                         ann._p(b2.copy()), ann._p(a2.copy()), None, ann._p(old.copy()),
+                                         ctypes.byref(e_out))
+    assert rc == ann._abi.ANN_EINVAL and b"unknown order" in ann._lib().ann_last_error()
 
 
 def test_index_file_keeps_the_id_map(tmp_path):
