@@ -1122,6 +1122,7 @@ struct WgCtl {
   int slot;                 // ring slot holding its block
   int len;                  // list length before this step's merge
   int plen;                 // pending-buffer length before this step's merge
+  int pf_slot;              // ring slot of the next node whose loads go out early, or -1
   int vis_count;            // visited-log entries of the query so far
   int cand_count;           // candidates entering the list this step
   int qi;                   // query the block works on
@@ -1272,6 +1273,47 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
     return pos0;
   };
 
+  // Next-node prefetch (depth >= 2), as in run_query: once this step's
+  // candidates are in, the next node's block has landed (warp 0 waits for
+  // it), and every warp issues the code gathers and visited-bit atomics of
+  // its share of that node's neighbours, so their round trip overlaps this
+  // step's sort and merge and the next step's selection.  The block barrier
+  // before them orders them after this node's atomics (whose results every
+  // warp has already used), so the visited set sees the same inserts in the
+  // same order.
+  const bool prefetch = D >= 2;
+  bool pre = false;
+  int pw[NBW];
+  unsigned pword[NBW], pold[NBW];
+  uint4 pcode[NBW][kMaxM / 16];
+  // this warp's share of the neighbours of the block at `b`: ids, code
+  // gathers, visited-bit atomics
+  auto issue_share = [&](const unsigned char* b, int (&w)[NBW], unsigned (&word)[NBW],
+                         uint4 (&code)[NBW][kMaxM / 16], unsigned (&old)[NBW]) {
+    const int32_t* nbr = reinterpret_cast<const int32_t*>(b + a.ids_off);
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      const int jj = t * 32 + lane;
+      const int j = warp * kChunk + jj;
+      int id = (jj < kChunk && j < a.R) ? nbr[j] : -1;
+      if (id >= n) id = -1;
+      w[t] = id;
+      word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < NBW; ++t) {
+      if (w[t] >= 0) {
+        const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
+#pragma unroll
+        for (int c = 0; c < kMaxM / 16; ++c)
+          if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NBW; ++t)
+      old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
+  };
+
   for (;;) {
     // ---- a3-a5 (warp 0): select, issue fetches, and wait for the oldest
     // when more than D are in flight or nothing is selectable
@@ -1379,34 +1421,26 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       result_insert(res, nres, k, make_key(warp_sum_u32(acc), static_cast<unsigned>(ctl->ukey)), lane);
     }
 
-    // ---- a7: this warp's neighbour positions and the visited set
-    const int32_t* nbr = reinterpret_cast<const int32_t*>(blk + a.ids_off);
+    // ---- a7: this warp's neighbour positions and the visited set (issued
+    // one step early when the node was prefetched)
     int w[NBW];
     unsigned word[NBW];
     bool fresh[NBW];
-#pragma unroll
-    for (int t = 0; t < NBW; ++t) {
-      const int jj = t * 32 + lane;
-      const int j = warp * kChunk + jj;
-      int id = (jj < kChunk && j < a.R) ? nbr[j] : -1;
-      if (id >= n) id = -1;
-      w[t] = id;
-      word[t] = id >= 0 ? static_cast<unsigned>(id) >> 5 : 0u;
-    }
     uint4 code[NBW][kMaxM / 16];
-#pragma unroll
-    for (int t = 0; t < NBW; ++t) {
-      if (w[t] >= 0) {
-        const uint4* cp = reinterpret_cast<const uint4*>(a.codes + static_cast<size_t>(w[t]) * a.M);
-#pragma unroll
-        for (int c = 0; c < kMaxM / 16; ++c)
-          if (c < (a.M >> 4)) code[t][c] = __ldg(cp + c);
-      }
-    }
     unsigned old[NBW];
+    if (pre) {
 #pragma unroll
-    for (int t = 0; t < NBW; ++t)
-      old[t] = w[t] >= 0 ? atomicOr(vis + word[t], 1u << (w[t] & 31)) : 0u;
+      for (int t = 0; t < NBW; ++t) {
+        w[t] = pw[t];
+        word[t] = pword[t];
+        old[t] = pold[t];
+#pragma unroll
+        for (int c = 0; c < kMaxM / 16; ++c) code[t][c] = pcode[t][c];
+      }
+      pre = false;
+    } else {
+      issue_share(blk, w, word, code, old);
+    }
 #pragma unroll
     for (int t = 0; t < NBW; ++t) fresh[t] = w[t] >= 0 && ((old[t] >> (w[t] & 31)) & 1u) == 0u;
     // ---- a8: asymmetric distances from the lookup table
@@ -1455,6 +1489,25 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       }
     }
     __syncthreads();  // every warp's candidates and log entries are in
+
+    // the next node's loads, overlapping the sort and merge below
+    if (prefetch) {
+      if (warp == 0) {
+        int ps = -1;
+        if (inflight >= 2) {
+          cp_async_wait_pending(inflight - 1);  // the next node's block (issued a step ago or more)
+          ps = head;
+        }
+        __syncwarp();
+        if (lane == 0) ctl->pf_slot = ps;
+      }
+      __syncthreads();  // its block is visible to every warp
+      const int ps = ctl->pf_slot;
+      if (ps >= 0) {
+        issue_share(ring + ps * slot_bytes, pw, pword, pcode, pold);
+        pre = true;
+      }
+    }
 
     // ---- a9: sort the candidates (warp 0), then merge them into the list
     // (all warps), or, for long lists, into the pending buffer (warp 0)
