@@ -46,7 +46,7 @@ DATA = os.path.join(ROOT, "_data")
 NCU_BYTES_PER_EXPANSION = {
     "search_kernel<PQ,2>": (420.0, 467.2),             # one warp per query, depth 1
     "search_kernel<PQ,2,prefetch>": (420.0, 480.6),    # depth >= 2, next-node prefetch
-    "search_kernel_wg<2,4>": (420.0, 464.8),           # a warp group of 4 per query
+    "search_kernel_wg<2,4>": (420.0, 470.4),           # a warp group of 4 per query (depth 2)
 }
 METRIC = "QPS at recall@10>=0.95 on 1 B300, relaxed vs sync search; p50/p99 latency"
 WORKLOAD = "out-of-core relaxed pipeline: 1M SIFT-like u8 d=128, 10k queries, Vamana R=64, PQ M=32 in HBM, 512 B node blocks in host pinned memory, k=10"
