@@ -1574,7 +1574,9 @@ __device__ void run_query_wg(const SearchArgs& a, const QueryJob& job, unsigned 
       job.dists[j] = ok ? static_cast<float>(static_cast<unsigned>(r >> 32)) : __int_as_float(0x7f800000);
     }
   }
-  clear_visited(vis, vlog, ctl->vis_count, log_cap, a.vis_words, lane, warp, W);
+  // a stop with a prefetched node left its visited bits out of the log:
+  // clear the whole table then, as run_query does
+  clear_visited(vis, vlog, pre ? log_cap + 1 : ctl->vis_count, log_cap, a.vis_words, lane, warp, W);
   if (warp == 0 && lane == 0) {
     if (job.steps) *job.steps = steps;
     if (job.status) *job.status = status;

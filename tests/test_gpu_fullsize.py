@@ -7,8 +7,9 @@ by the oracle and must match bit-exactly (ids, distances, step counts).
 The index (graph, codebook, codes) comes from the library's host-side
 construction tooling (ann_build_graph / ann_build_pq, plain C++ threads, no
 GPU); it is input data for both sides and is cached under _data/.  It is
-the index the benchmark times (its default builder), and L=1280 at depths 1
-and 0 is the benchmark's operating point on it.
+the index the benchmark times (its default builder); L=1280 is the
+benchmark's operating point on it, timed at depths 0, 1 and 2 with one or
+more warps per query (the benchmark keeps the fastest).
 """
 import numpy as np
 import pytest
@@ -31,10 +32,12 @@ def sift1m():
     ix.close()
 
 
-@pytest.mark.parametrize("L,depth", [(1280, 1), (1280, 0), (1536, 1), (128, 4)])
-def test_full_batch_sampled_against_oracle(sift1m, L, depth):
+@pytest.mark.parametrize("L,depth,wpq", [(1280, 2, 1), (1280, 2, 4), (1280, 1, 1), (1280, 0, 1),
+                                          (1536, 1, 1), (128, 4, 1)])
+def test_full_batch_sampled_against_oracle(sift1m, L, depth, wpq):
     import torch
     w, ix = sift1m
+    ix.set_warps_per_query(wpq)
     nq, k = w["q"].shape[0], 10
     q = torch.from_numpy(w["q"]).cuda()
     ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
@@ -43,6 +46,7 @@ def test_full_batch_sampled_against_oracle(sift1m, L, depth):
     st = torch.cuda.Stream()
     ix.search_dev(q, k, L, depth, ids, dists, stream=st, trace={"steps": steps})
     stats = ix.sync(st)
+    ix.set_warps_per_query(1)
     assert stats.n_failed == 0
     ids, dists, steps = ids.cpu().numpy(), dists.cpu().numpy(), steps.cpu().numpy()
     oi, od, os_ = oracle.search(w["base"], w["adj"], w["entry"], w["q"][SAMPLE], k, L, depth,

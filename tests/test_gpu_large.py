@@ -1,8 +1,10 @@
 """Out-of-core search at 10^8 nodes: 51.2 GB of 512-byte node blocks in host
 pinned memory, 3.2 GB of PQ codes in HBM, 10,000 queries in one batch at
-L=128 and depths 0 and 1.  Sampled queries must match the oracle bit-exactly
-(ids, distances, step counts); every query must give sorted distances equal
-to the exact integer L2 of its ids.
+L=128 and depths 0 and 1, and in the launch configuration the benchmark's
+10^8 operating point uses (L=5120, depth 4, a group of 4 warps per query).
+Sampled queries must match the oracle bit-exactly (ids, distances, step
+counts); every query must give sorted distances equal to the exact integer L2
+of its ids.
 
 The index is a random-link sample index (R=64 uniform neighbour ids, uniform
 random uint8 vectors and PQ codes, an integer codebook), the kind the degree
@@ -60,18 +62,20 @@ def large():
     ix.close()
 
 
-@pytest.mark.parametrize("depth", [1, 0])
-def test_large_batch_against_oracle(large, depth):
+@pytest.mark.parametrize("L,depth,wpq", [(128, 1, 1), (128, 0, 1), (5120, 4, 4)])
+def test_large_batch_against_oracle(large, L, depth, wpq):
     import torch
     w = large
-    k, L = 10, 128
+    k = 10
     q = torch.from_numpy(w["q"]).cuda()
     ids = torch.empty((NQ, k), dtype=torch.int32, device="cuda")
     dists = torch.empty((NQ, k), dtype=torch.float32, device="cuda")
     steps = torch.empty(NQ, dtype=torch.int32, device="cuda")
     st = torch.cuda.Stream()
+    w["ix"].set_warps_per_query(wpq)
     w["ix"].search_dev(q, k, L, depth, ids, dists, stream=st, trace={"steps": steps})
     stats = w["ix"].sync(st)
+    w["ix"].set_warps_per_query(1)
     assert stats.n_failed == 0
     ids, dists, steps = ids.cpu().numpy(), dists.cpu().numpy(), steps.cpu().numpy()
     oi, od, os_ = oracle.search(w["base"], w["adj"], 0, w["q"][SAMPLE], k, L, depth,
